@@ -1,0 +1,397 @@
+"""Benchmark of the shaken-dynamics hot path on GB300.
+
+Workload (one GPU): one 16384 x 16384 bit-packed torus pair (2.7e8 sites per
+sublattice), random start (init seed 3), q = 1.0, J = 0.35, Philox seed 3,
+2000 full steps with the five observable sums of every step.  One benchmark
+step is 100 full steps through shk_run (2 * 16384^2 * 100 = 5.4e10 site
+updates); the default 20 timed steps cover the 2000 full steps once.
+
+Metric: site updates per second (one site update = one spin redrawn in one
+half-step).  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own replica lattice (lattice id =
+rank) with no data exchange; the timed region is bracketed by barriers and the
+slowest rank's time is used.  --impl reference times the single-threaded CPU
+oracle (the paper gives no runnable code) on a bounded row band of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L = 16384
+Q, J = 1.0, 0.35
+SEED = 3
+INIT_SEED = 3
+STEPS_PER_BENCH_STEP = 100
+TOTAL_STEPS = 2000
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = ("shaken dynamics, one 16384x16384 bit-packed torus pair, random start, "
+            "q=1.0, J=0.35, seed 3, 2000 full steps, per-step M/E/C_nn sums")
+METRIC = "site updates/s at L=16384 (bit-packed, 2000 full steps)"
+UNIT = "site updates/s"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT = 152
+MAX_SM_MHZ = 2070.0
+
+
+def _peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", MAX_SM_MHZ)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, MAX_SM_MHZ, "fallback"
+
+
+def _expected_algorithmic_ops_per_block():
+    """Integer ops one 32-site block needs under the lazy most-significant-bit-
+    first comparison, assuming per-block early exit: P = number of random
+    planes until all 32 sites are decided (each plane settles a site with
+    probability 1/2, so P(P <= b) = (1 - 2^-b)^32, P <= 32), ceil(P/4) Philox
+    calls of 40 ops (10 rounds x (2 wide multiplies + 2 three-input xors)) and
+    6 bitwise ops per plane."""
+    e_planes = 0.0
+    e_calls = 0.0
+    prev = 0.0
+    for b in range(1, 33):
+        cdf = (1.0 - 2.0 ** -b) ** 32 if b < 32 else 1.0
+        pb = cdf - prev
+        prev = cdf
+        e_planes += b * pb
+        e_calls += ((b + 3) // 4) * pb
+    return 40.0 * e_calls + 6.0 * e_planes, e_planes, e_calls
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"shk_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < len(self.FIELDS):
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- oracle timing
+
+def _oracle_sample_rate(rows: int, reps: int = 1):
+    """Site updates/s of the single-threaded CPU oracle doing half-steps A and B
+    on rows [0, rows) of the L = 16384 workload; returns (rate, seconds, units)."""
+    import numpy as np
+    from oracle import oracle as orc
+
+    rng = np.random.default_rng(SEED)
+    sigma = np.where(rng.random(L * L, dtype=np.float32) < 0.5, 1, -1).astype(np.int8)
+    tau = np.empty_like(sigma)
+    T = orc.thresholds(Q, J)
+    units = 0
+    t0 = time.perf_counter()
+    for r in range(reps):
+        orc.halfstep(0, sigma, L, T, SEED, 0, 2 * r, 0, rows, dst=tau)
+        orc.halfstep(1, tau, L, T, SEED, 0, 2 * r + 1, 0, rows, dst=sigma)
+        units += 2 * rows * L
+    dt = time.perf_counter() - t0
+    return units / dt, dt, units
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return 0
+    rows = 512
+    import numpy as np
+    from oracle import oracle as orc
+
+    rng = np.random.default_rng(SEED)
+    sigma = np.where(rng.random(L * L, dtype=np.float32) < 0.5, 1, -1).astype(np.int8)
+    tau = np.empty_like(sigma)
+    T = orc.thresholds(Q, J)
+
+    def one_step(t):
+        orc.halfstep(0, sigma, L, T, SEED, 0, 2 * t, 0, rows, dst=tau)
+        orc.halfstep(1, tau, L, T, SEED, 0, 2 * t + 1, 0, rows, dst=sigma)
+
+    for w in range(args.warmup):
+        one_step(w)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one_step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    units = args.steps * 2 * rows * L
+    value = units / dt
+    sample = (f"half-steps A and B on rows 0..{rows - 1} of the 16384x16384 torus per step "
+              f"({2 * rows * L} site updates), single-threaded C oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "layout": "int8 (oracle)", "rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+
+    from paper_1908_07341_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1908_07341_gb300 as shk
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def bench_layout(layout: str, steps: int, warmup: int, with_e2e: bool):
+        lat = shk.Lattice(L, layout, device=dev, stream=stream)
+        lat.set_seed(SEED, rank).set_params(Q, J).init("random", init_seed=INIT_SEED)
+        obs = torch.empty((STEPS_PER_BENCH_STEP, shk.NOBS), dtype=torch.int64, device=dev)
+        for _ in range(warmup):
+            lat.run(STEPS_PER_BENCH_STEP, obs)
+        # the timed steps start the configured run from its initial state:
+        # 20 benchmark steps are exactly the 2000 full steps of the workload
+        lat.init("random", init_seed=INIT_SEED)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier()
+        for k in range(steps):
+            flush.fill_(k & 0xFF)               # evict L2 between timed steps (not timed)
+            starts[k].record(stream)
+            lat.run(STEPS_PER_BENCH_STEP, obs)
+            ends[k].record(stream)
+        barrier()
+        ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+        e2e = None
+        if with_e2e:
+            # End to end through the public API with host buffers: upload sigma
+            # from pinned host memory, run, read the step's observables back.
+            raw = L * L // 8 if layout == "bitpack" else L * L
+            host_sigma = torch.empty(raw, dtype=torch.uint8, pin_memory=True)
+            lat.download_plane(0, host_sigma)
+            host_obs = torch.empty((STEPS_PER_BENCH_STEP, shk.NOBS), dtype=torch.int64, pin_memory=True)
+            torch.cuda.synchronize()
+            barrier()
+            e_start = torch.cuda.Event(enable_timing=True)
+            e_end = torch.cuda.Event(enable_timing=True)
+            n_e2e = max(1, steps // 2)
+            t_host0 = time.perf_counter()
+            e_start.record(stream)
+            for _ in range(n_e2e):
+                lat.upload_plane(0, host_sigma)
+                lat.run(STEPS_PER_BENCH_STEP, obs)
+                host_obs.copy_(obs, non_blocking=True)
+                stream.synchronize()
+            e_end.record(stream)
+            barrier()
+            e_ms = e_start.elapsed_time(e_end)
+            host_ms = 1e3 * (time.perf_counter() - t_host0)
+            e2e = {"ms": max(e_ms, host_ms), "steps": n_e2e, "h2d": raw, "d2h": int(obs.numel() * 8)}
+        # dominant kernel: the two half-step sweeps, timed launch by launch with
+        # events on the launching stream, same planes and grid as inside shk_run
+        T = shk.thresholds(Q, J)
+        src, dst = lat.plane(0), lat.plane(1)
+        acc = torch.zeros(shk.NOBS, dtype=torch.int64, device=dev)
+        kern_ms = []
+        for rep in range(3 + 20):
+            half = rep & 1
+            a, b = (src, dst) if half == 0 else (dst, src)
+            s_ev = torch.cuda.Event(enable_timing=True)
+            e_ev = torch.cuda.Event(enable_timing=True)
+            s_ev.record(stream)
+            shk.halfstep(layout, half, a, b, L, T, SEED, rank, 2 * 4000 + rep, acc, stream)
+            e_ev.record(stream)
+            if rep >= 3:
+                kern_ms.append((s_ev, e_ev))
+        torch.cuda.synchronize()
+        kern = [s.elapsed_time(e) for s, e in kern_ms]
+        lat.close()
+        return ms, e2e, sum(kern) / len(kern)
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    t_wall0 = time.perf_counter()
+    ms, e2e, kern_ms = bench_layout("bitpack", args.steps, args.warmup, with_e2e=True)
+    wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop() if sampler else None
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = max_over_ranks(ms)
+    units_per_step = 2 * L * L * STEPS_PER_BENCH_STEP
+    value = world * units_per_step * args.steps / (ms / 1e3)
+    e2e_ms = max_over_ranks(e2e["ms"])
+    e2e_value = world * units_per_step * e2e["steps"] / (e2e_ms / 1e3)
+
+    # secondary line: the int8 layout on the same workload (fewer steps)
+    ms8, _, kern8_ms = bench_layout("int8", max(2, args.steps // 5), 1, with_e2e=False)
+    ms8 = max_over_ranks(ms8)
+    value8 = world * units_per_step * max(2, args.steps // 5) / (ms8 / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    hbm_gbs, sm_max, peak_kind = _peaks()
+    ops_block, e_planes, e_calls = _expected_algorithmic_ops_per_block()
+    sites_per_launch = L * L
+    alu_ops = ops_block * (sites_per_launch / 32)
+    alu_peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12          # Tops/s, issue slots at max clock
+    alu_achieved = alu_ops / (kern_ms / 1e3) / 1e12
+    hbm_bytes_bp = 2 * sites_per_launch / 8                  # read 1 bit + write 1 bit per site
+    hbm_bytes_i8 = 2 * sites_per_launch                      # read 1 byte + write 1 byte per site
+    traffic = _load_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "layout": "bitpack", "q": Q, "J": J, "seed": SEED,
+                   "full_steps_per_bench_step": STEPS_PER_BENCH_STEP,
+                   "site_updates_per_bench_step": units_per_step,
+                   "l2": "flushed between timed steps (256 MiB write); both planes (64 MiB) fit in L2 "
+                         "during a step", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                "d2h_bytes_per_step": e2e["d2h"]},
+        "gpu_launches": args.steps * (2 * STEPS_PER_BENCH_STEP + 1),
+        "roofline": {
+            "bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
+            "frac": alu_achieved / alu_peak, "traffic": traffic.get("k_sweep_bp"),
+            "kernel": "k_sweep_bp (half-step A/B)", "kernel_ms": kern_ms,
+            "peak_basis": f"{SM_COUNT} SMs x 128 issue lanes x {sm_max:.0f} MHz (derived)",
+            "algorithmic_ops_per_32_sites": ops_block,
+            "hbm": {"achieved": hbm_bytes_bp / (kern_ms / 1e3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": hbm_bytes_bp / (kern_ms / 1e3) / 1e9 / hbm_gbs, "peak_kind": peak_kind},
+        },
+        "int8": {"value": value8, "unit": UNIT, "steps": max(2, args.steps // 5),
+                 "roofline": {"bound": "hbm", "achieved": hbm_bytes_i8 / (kern8_ms / 1e3) / 1e9,
+                              "peak": hbm_gbs, "unit": "GB/s",
+                              "frac": hbm_bytes_i8 / (kern8_ms / 1e3) / 1e9 / hbm_gbs,
+                              "traffic": traffic.get("k_sweep_i8"), "kernel_ms": kern8_ms,
+                              "peak_kind": peak_kind}},
+        "clocks": clocks,
+        "wall_s_bitpack": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rows = 8192
+        rate, secs, units = _oracle_sample_rate(rows)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"half-steps A and B on rows 0..{rows - 1} of the 16384x16384 torus "
+                      f"({units} site updates, {secs:.1f} s), single-threaded C oracle"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _load_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if present and
+    taken on the current kernels (see profiles/)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

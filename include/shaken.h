@@ -1,0 +1,216 @@
+/*
+ * shaken.h -- C ABI of the GB300 shaken-dynamics library (libshaken.so).
+ *
+ * The shaken dynamics (D'Autilia, Andrianaivo, Troiani, arXiv:1908.07341,
+ * Section 2) is a probabilistic cellular automaton on two L x L periodic
+ * sublattices: sigma on Lambda_1 and tau on Lambda_2.  One full step is two
+ * synchronous half-steps in which every spin of one sublattice is redrawn
+ * independently given the other (Eq. "fact"):
+ *
+ *   half-step A (Eq. "leftTrans"):  P(tau_x = +1 | sigma) = e^{h}/(2 cosh h),
+ *        h = <-h_x(sigma) = J (sigma_{x down} + sigma_{x left}) + q sigma_x
+ *   half-step B (Eq. "rightTrans"): P(sigma_x = +1 | tau) = e^{h}/(2 cosh h),
+ *        h = ->h_x(tau)   = J (tau_{x up} + tau_{x right}) + q tau_x
+ *
+ * with x = (i, j), x^up = (i, j+1), x^right = (i+1, j), x^down = (i, j-1),
+ * x^left = (i-1, j) on the torus (Section 2) and (q, J) already multiplied by
+ * beta (Section 2, "rescaling the interactions").
+ *
+ * Conventions fixed by this library (identical in the CPU oracle):
+ *   - site index u = j*L + i (row j, column i);
+ *   - SHK_INT8 planes: one int8 per site, +1 or -1, at byte u;
+ *   - SHK_BITPACK planes: uint32 word w = u >> 5 holds sites 32w..32w+31,
+ *     bit p = u & 31 (least significant bit = smallest u), bit set iff +1;
+ *     requires L % 32 == 0 so that every row is a whole number of words;
+ *   - step t (0-based) is half-step A with half-step index hs = 2t followed
+ *     by half-step B with hs = 2t + 1 (the order of Eqs. leftTrans/rightTrans);
+ *   - the draw is "+1 iff r < T[k]" with a 32-bit uniform r per site and the
+ *     integer threshold table of shk_thresholds(); the uniform of site u is
+ *     built from Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed,
+ *     counter (hs, u >> 5, lattice_id, c), c = 0..7: the 32 output words
+ *     R[0..31] of the 32-site block form a 32 x 32 bit matrix and
+ *     r(u) = sum_b bit_{u & 31}(R[b]) 2^(31-b).  Trajectories are therefore a
+ *     pure function of (initial state, q, J, seed, lattice_id, t).
+ *   - observables of step t are exact int64 sums on the pair (sigma_t, tau_t)
+ *     at the end of the step (Section 3.1 magnetisation; Eq. "gs_ham2"):
+ *       [0] M_sigma = sum sigma_x            [1] M_tau = sum tau_x
+ *       [2] S_q     = sum sigma_x tau_x
+ *       [3] S_J     = sum sigma_x (tau_{x up} + tau_{x right})
+ *       [4] C_nn    = sum sigma_x (sigma_{x up} + sigma_{x right})
+ *     so m = M_sigma / L^2 and H(sigma_t, tau_t) = -(J S_J + q S_q).
+ *
+ * Memory and threads: device memory is always owned by the caller (for
+ * example PyTorch tensors); the library never allocates or frees device
+ * memory.  Host buffers are caller-owned.  Work is enqueued asynchronously on
+ * the caller's CUDA stream (passed as void*, NULL = legacy default stream);
+ * only the shk_read_* / shk_write_* calls synchronise that stream.  A handle
+ * must not be used from two host threads at once.  No C++ exception and no
+ * abort crosses this interface: every function returns a status code and
+ * leaves a message for shk_last_error().
+ */
+#ifndef SHAKEN_H
+#define SHAKEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define SHK_OK          0
+#define SHK_EINVAL    (-1)  /* an argument is out of range (message says which) */
+#define SHK_ENOMEM    (-2)  /* a caller buffer is smaller than required          */
+#define SHK_ECUDA     (-3)  /* a CUDA runtime call or kernel launch failed        */
+#define SHK_ESTATE    (-4)  /* the handle is not ready (e.g. q, J never set)      */
+#define SHK_EBUSY     (-5)  /* no free capacity; retry later (never blocks)       */
+#define SHK_ETIMEOUT  (-6)  /* a bounded wait gave up                             */
+#define SHK_ECANCELLED (-7) /* the job was cancelled                              */
+
+/* ------------------------------------------------------------ enumerations */
+#define SHK_BITPACK 1
+#define SHK_INT8    2
+
+#define SHK_INIT_ALL_UP   0
+#define SHK_INIT_ALL_DOWN 1
+#define SHK_INIT_RANDOM   2   /* each spin +1 with probability 1/2 */
+
+#define SHK_HALF_A 0          /* sigma -> tau, left field (Eq. leftTrans)  */
+#define SHK_HALF_B 1          /* tau -> sigma, right field (Eq. rightTrans) */
+
+#define SHK_NOBS 5
+#define SHK_OBS_M_SIGMA 0
+#define SHK_OBS_M_TAU   1
+#define SHK_OBS_S_Q     2
+#define SHK_OBS_S_J     3
+#define SHK_OBS_C_NN    4
+
+#define SHK_MAX_L 262144      /* largest side accepted (2^18)                  */
+#define SHK_MAX_STEP 0x80000000ull  /* step indices t must stay below 2^31     */
+
+/* ------------------------------------------------------------ diagnostics */
+
+/* Static English text for a status code. */
+const char* shk_strerror(int status);
+
+/* Message of the last failing call on this handle, or, for handle == NULL,
+ * of the last failing handle-free call made by this host thread.  The string
+ * is owned by the library and valid until the next call on the same handle
+ * (or thread). */
+const char* shk_last_error(const void* handle);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int shk_version(void);
+
+/* ------------------------------------------------------------ thresholds */
+
+/* The six integer thresholds of the per-site draw (Algorithm 3: "+1 iff
+ * rand() < e^h / (2 cosh h)"), indexed k = 3*[s = +1] + n, where s is the
+ * spin of the site itself and n in {0, 1, 2} the number of +1 neighbours in
+ * the field, so that h = q*s + J*(2n - 2).  For h > 0,
+ * T = min(2^32 - 1, floor(2^32 / (1 + e^{-2h}))) in IEEE double; for h < 0,
+ * T(h) = 2^32 - T(-h); T(0) = 2^31.  Hence T[k] + T[5-k] = 2^32 whenever the
+ * field is non-zero, and P(+1) = T[k] / 2^32 exactly.
+ * Host-only (no GPU needed).  Returns SHK_EINVAL for non-finite q or J or a
+ * NULL out. */
+int shk_thresholds(double q, double J, uint32_t out[6]);
+
+/* ------------------------------------------------------------ stateless hot path */
+
+/* Bytes of one spin plane of side L in the given layout (0 if invalid). */
+size_t shk_plane_bytes(int L, int layout);
+
+/* One synchronous half-step over a whole L x L plane (Eq. leftTrans for
+ * half = SHK_HALF_A, Eq. rightTrans for half = SHK_HALF_B; the sites are
+ * independent given src, Eq. "fact").
+ *   src, dst   device pointers to distinct planes of shk_plane_bytes(L, layout)
+ *              bytes: for A src = sigma, dst = tau; for B src = tau, dst = sigma.
+ *   T          host array of six thresholds satisfying T[k] + T[5-k] = 2^32
+ *              (as produced by shk_thresholds; SHK_EINVAL otherwise).
+ *   seed, lattice_id, hs   key and counter words of the random numbers
+ *              (hs = 2t for A of step t, 2t + 1 for B).
+ *   obs_accum  nullable device array of SHK_NOBS int64 to which the fused
+ *              reductions are ADDED (the caller zeroes it): A adds M_tau of dst
+ *              to [1] and sum src_x (src_{x down} + src_{x left}), which equals
+ *              C_nn of src, to [4]; B adds M_sigma of dst to [0], S_q to [2],
+ *              S_J to [3].
+ *   stream     cudaStream_t as void*.
+ * Asynchronous.  Layout SHK_BITPACK requires L % 32 == 0; SHK_INT8 accepts
+ * any 2 <= L <= SHK_MAX_L. */
+int shk_halfstep(int layout, int half, const void* src, void* dst, int L,
+                 const uint32_t T[6], uint64_t seed, uint32_t lattice_id,
+                 uint32_t hs, int64_t* obs_accum, void* stream);
+
+/* Fills a device plane with an initial state: all +1, all -1 or random
+ * (+1 iff the site uniform of counter (plane_index, u >> 5, lattice_id,
+ * 256 + c) under key init_seed is below 2^31).  Asynchronous. */
+int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
+                   uint32_t lattice_id, uint32_t plane_index, void* stream);
+
+/* ------------------------------------------------------------ lattice handle */
+
+typedef struct shk_lattice shk_lattice;
+
+/* Device bytes a lattice of side L needs: both planes plus a 256-byte
+ * observable ring.  0 if (L, layout) is invalid. */
+size_t shk_lattice_bytes(int L, int layout);
+
+/* Creates a handle over caller-owned device memory dev_mem (at least
+ * shk_lattice_bytes(L, layout) bytes, 256-byte aligned, kept alive by the
+ * caller until shk_lattice_destroy).  The planes start undefined: call
+ * shk_lattice_init or shk_write_spins.  Errors: SHK_EINVAL (bad L, layout,
+ * alignment or NULL), SHK_ENOMEM (bytes too small). */
+int shk_lattice_create(int L, int layout, void* dev_mem, size_t bytes, void* stream,
+                       shk_lattice** out);
+
+/* Releases the host-side handle; the device memory stays the caller's. */
+void shk_lattice_destroy(shk_lattice* lat);
+
+/* Sets sigma and tau to an initial state (see shk_init_plane; plane 0 is
+ * sigma, plane 1 is tau) and the step counter to 0.  Only sigma matters for
+ * the dynamics: half-step A overwrites tau without reading it. */
+int shk_lattice_init(shk_lattice* lat, int kind, uint64_t init_seed);
+
+/* Sets (q, J) (already rescaled by beta) and rebuilds the threshold table.
+ * Non-finite values give SHK_EINVAL. */
+int shk_set_params(shk_lattice* lat, double q, double J);
+
+/* Sets the Philox key (seed) and the lattice id (third counter word). */
+int shk_set_seed(shk_lattice* lat, uint64_t seed, uint32_t lattice_id);
+
+/* Step counter t of the next step to run (checkpoint / resume: the state
+ * after step t-1 plus (q, J, seed, lattice_id, t) determines the future). */
+int shk_set_step(shk_lattice* lat, uint64_t step);
+int shk_get_step(const shk_lattice* lat, uint64_t* step);
+
+/* Runs n_steps full steps t, t+1, ..., t+n_steps-1 and advances the step
+ * counter.  dev_obs, if not NULL, is a device array of n_steps * SHK_NOBS
+ * int64 that receives the observables of every step (row s = step t+s).
+ * Asynchronous on the handle's stream.  Errors: SHK_ESTATE if q, J were never
+ * set, SHK_EINVAL if the step counter would reach SHK_MAX_STEP. */
+int shk_run(shk_lattice* lat, uint64_t n_steps, int64_t* dev_obs);
+
+/* Copies the observables of the last completed step to host_out (synchronises
+ * the stream).  SHK_ESTATE if no step has run since the last init/write. */
+int shk_read_observables(shk_lattice* lat, int64_t host_out[SHK_NOBS]);
+
+/* Host <-> device spin transfer as int8 +/-1 arrays of L*L entries (u = j*L+i),
+ * whatever the device layout; plane 0 = sigma, 1 = tau.  Synchronous. */
+int shk_read_spins(shk_lattice* lat, int plane, int8_t* host_out);
+int shk_write_spins(shk_lattice* lat, int plane, const int8_t* host_in);
+
+/* Raw transfer of one plane in its device layout (shk_plane_bytes bytes),
+ * host buffer caller-owned (pinned memory makes it asynchronous).  Enqueued on
+ * the handle's stream; does not synchronise. */
+int shk_upload_plane(shk_lattice* lat, int plane, const void* host_raw, size_t bytes);
+int shk_download_plane(shk_lattice* lat, int plane, void* host_raw, size_t bytes);
+
+/* Device pointer of plane 0 (sigma) or 1 (tau) inside the handle's memory. */
+void* shk_plane_ptr(shk_lattice* lat, int plane);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHAKEN_H */

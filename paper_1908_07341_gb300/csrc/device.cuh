@@ -1,0 +1,192 @@
+// device.cuh -- device building blocks of the shaken-dynamics half-step.
+//
+// A half-step (Eqs. leftTrans / rightTrans of arXiv:1908.07341) redraws every
+// spin of one sublattice independently, +1 with probability
+// e^h / (2 cosh h), h the left or right local field (Eq. urdl).  The library
+// realises the draw as "r < T[k]" with a 32-bit site uniform r and the integer
+// threshold T[k] of the site's field class k = 3*[s = +1] + n (s the site's
+// own spin, n the number of +1 neighbours in the field).
+//
+// GB300 design: spins are processed 32 at a time as bit-sliced words.  The 32
+// uniforms of a 32-site block are the columns of the 32 x 32 bit matrix whose
+// rows are the block's 32 Philox4x32-10 output words, most significant bit
+// first.  Comparing 32 uniforms with 32 thresholds is then a bit-serial
+// comparison from the most significant bit down: plane b of the random matrix
+// is one Philox word, and each plane settles every still-undecided site with
+// probability 1/2.  Planes (and the Philox calls that produce them, four per
+// call) are generated only while some site of the warp is still undecided:
+// about 13 of the 32 planes on average, so 3.2 instead of 8 Philox calls per
+// block, with results identical bit for bit to the full comparison.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace shk {
+
+// Philox4x32 round multipliers and Weyl key increments (Salmon et al., 2011).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+
+constexpr int kNumObs = 5;
+
+// Everything a half-step needs besides the spins: the ten Philox round keys of
+// the seed and, per random plane b = 0..31 (bit 31-b of the thresholds), the
+// bit masks that select the threshold bit of each field class.  With the
+// complement rule T[k] + T[5-k] = 2^32 only the three thresholds of a + site,
+// U[n'] = T[3 + n'], are needed: a - site with n up-neighbours compares the
+// complemented uniform against U[2 - n] and takes the complemented result.
+// n' counts the neighbours that agree with the site.
+struct DrawParams {
+    uint32_t rk0[10];     // seed_lo + r * W0
+    uint32_t rk1[10];     // seed_hi + r * W1
+    uint32_t m0[32];      // all ones iff bit (31-b) of U[0] is set
+    uint32_t d01[32];     // m0 ^ m1
+    uint32_t d12[32];     // m1 ^ m2
+    uint32_t lattice_id;  // third counter word
+    uint32_t c3_base;     // fourth counter word of call 0 (256 * domain)
+};
+
+// Philox4x32-10 on the counter (c0, c1, c2, c3) with precomputed round keys.
+// The caller puts the per-thread block index in c1: the first round's two
+// products then involve only block-uniform words.
+template <class PP>
+__device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                         const PP& P) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = kPhiloxM0 * c0;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+        const uint32_t lo1 = kPhiloxM1 * c2;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ P.rk0[r];
+        const uint32_t n2 = hi0 ^ c3 ^ P.rk1[r];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+}
+
+// Draws the 32 spins of block w (sites 32w .. 32w+31).
+//   S      bits of the sites themselves in the source plane (1 = +1)
+//   A, B   bits of the two field neighbours of each site
+//   valid  sites that exist (bits beyond the plane are 0 and never delay exit)
+//   hs     half-step index (first counter word)
+// All 32 lanes of the warp must call this together: the loop over random
+// planes stops when no lane has an undecided valid site.
+template <class PP>
+__device__ __forceinline__ uint32_t draw_block(uint32_t S, uint32_t A, uint32_t B, uint32_t w,
+                                               uint32_t valid, uint32_t hs, const PP& P) {
+    const uint32_t F = ~S;                 // sites that are -1
+    const uint32_t a1 = ~(A ^ S);          // neighbour A agrees with the site
+    const uint32_t a2 = ~(B ^ S);
+    const uint32_t C2 = a1 & a2;           // both neighbours agree
+    const uint32_t Cg = a1 | a2;           // at least one agrees
+    uint32_t und = valid;                  // not yet decided
+    uint32_t up = 0;                       // decided +1
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t x0 = hs, x1 = w, x2 = P.lattice_id, x3 = P.c3_base + (uint32_t)c;
+        philox10(x0, x1, x2, x3, P);
+        const uint32_t R[4] = {x0, x1, x2, x3};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int b = 4 * c + m;
+            const uint32_t x = R[m];
+            // g: the raw random bit value that would decide the site as +1,
+            // i.e. the class threshold bit, complemented for - sites.
+            const uint32_t g = F ^ P.m0[b] ^ (Cg & P.d01[b]) ^ (C2 & P.d12[b]);
+            up |= und & ~x & g;
+            und &= ~(x ^ g);
+        }
+        if (c < 7 && !__any_sync(0xffffffffu, und != 0u)) break;
+    }
+    // A uniform equal to its threshold is not below it: + sites stay -1 ... and
+    // - sites (compared through the complement) come out +1.
+    return up | (und & F);
+}
+
+// ---------------------------------------------------------------- int8 <-> bits
+
+// Up-bits of the four int8 spins (+1 = 0x01, -1 = 0xFF) of one 32-bit word:
+// bit k of the result is 1 iff byte k is +1 (its sign bit is clear).
+__device__ __forceinline__ uint32_t pack_up4(uint32_t x) {
+    return (((~x) & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+__device__ __forceinline__ uint32_t pack_up32(const uint4& lo, const uint4& hi) {
+    return pack_up4(lo.x) | (pack_up4(lo.y) << 4) | (pack_up4(lo.z) << 8) |
+           (pack_up4(lo.w) << 12) | (pack_up4(hi.x) << 16) | (pack_up4(hi.y) << 20) |
+           (pack_up4(hi.z) << 24) | (pack_up4(hi.w) << 28);
+}
+
+// Four int8 spins from the low four bits of nib (bit k -> byte k).
+__device__ __forceinline__ uint32_t unpack4(uint32_t nib) {
+    const uint32_t y = (nib * 0x00204081u) & 0x01010101u;
+    return ~(y * 0xFEu);
+}
+
+__device__ __forceinline__ void unpack32(uint32_t bits, uint4& lo, uint4& hi) {
+    lo.x = unpack4(bits & 0xFu);
+    lo.y = unpack4((bits >> 4) & 0xFu);
+    lo.z = unpack4((bits >> 8) & 0xFu);
+    lo.w = unpack4((bits >> 12) & 0xFu);
+    hi.x = unpack4((bits >> 16) & 0xFu);
+    hi.y = unpack4((bits >> 20) & 0xFu);
+    hi.z = unpack4((bits >> 24) & 0xFu);
+    hi.w = unpack4(bits >> 28);
+}
+
+// ---------------------------------------------------------------- division
+
+// Division by a fixed divisor d >= 1 for n < 2^31: q = (umulhi(n, m) + n) >> s
+// with s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+    uint32_t d, m, s;
+};
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+    return (__umulhi(n, f.m) + n) >> f.s;
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum64(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Adds per-thread values v[0..NV) of the whole block into dst[idx[i]] with one
+// 64-bit atomic per value per block.  All threads of the block must call it.
+template <int NV>
+__device__ __forceinline__ void block_accumulate(const int (&v)[NV], long long* const (&dst)[NV]) {
+    __shared__ long long red[NV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int s = warp_sum(v[i]);
+        if (lane == 0) red[i][warp] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            long long s = lane < nwarps ? red[i][lane] : 0;
+            s = warp_sum64(s);
+            if (lane == 0 && dst[i] != nullptr)
+                atomicAdd(reinterpret_cast<unsigned long long*>(dst[i]),
+                          static_cast<unsigned long long>(s));
+        }
+    }
+}
+
+}  // namespace shk

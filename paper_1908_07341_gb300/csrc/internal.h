@@ -1,0 +1,63 @@
+// internal.h -- host-side interface between the C ABI (api.cu) and the
+// kernel launchers (kernels.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace shk {
+
+constexpr int kBitpack = 1;
+constexpr int kInt8 = 2;
+
+// Geometry of one L x L plane in a layout.
+struct Geometry {
+    int L = 0;
+    int layout = 0;
+    int64_t N = 0;          // L * L sites
+    uint32_t nblocks = 0;   // 32-site blocks: ceil(N / 32)
+    uint32_t Wr = 0;        // bit-packed words (32-site blocks) per row, L % 32 == 0 only
+    bool aligned = false;   // L % 32 == 0
+    size_t plane_bytes = 0; // device bytes of one plane (padded to 256)
+};
+
+bool make_geometry(int L, int layout, Geometry* g);
+FastDiv make_fastdiv(uint32_t d);
+
+// Host-side threshold table (own implementation of the rule in shaken.h).
+int host_thresholds(double q, double J, uint32_t out[6]);
+
+// Draw parameters for a seed / lattice id / table; false if the table breaks
+// the complement rule T[k] + T[5-k] = 2^32.
+bool make_draw_params(uint64_t seed, uint32_t lattice_id, const uint32_t T[6], uint32_t domain,
+                      DrawParams* P);
+
+// One half-step over a plane.  obs_cur receives the reductions of the drawn
+// plane (A: M_tau at [1]; B: M_sigma [0], S_q [2], S_J [3]); obs_prev (A only,
+// nullable) receives C_nn of the source plane at [4]; zero_slot (nullable)
+// is cleared by the launch (five int64).
+cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* dst,
+                            const DrawParams& P, uint32_t hs, long long* obs_cur,
+                            long long* obs_prev, long long* zero_slot, cudaStream_t st);
+
+// C_nn of a sigma plane added to obs[4].
+cudaError_t launch_cnn(const Geometry& g, const void* sigma, long long* obs, cudaStream_t st);
+
+// Initial state of one plane.
+cudaError_t launch_init(const Geometry& g, void* plane, int kind, uint64_t init_seed,
+                        uint32_t lattice_id, uint32_t plane_index, cudaStream_t st);
+
+// Whole run of n steps inside one CTA (both planes in shared memory).
+// obs (nullable) gets n rows of five sums; last gets the last row.
+bool small_path_fits(const Geometry& g);
+cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const DrawParams& P,
+                             uint64_t t0, uint64_t n, long long* obs, long long* last,
+                             cudaStream_t st);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+
+}  // namespace shk

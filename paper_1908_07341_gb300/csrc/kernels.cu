@@ -1,0 +1,604 @@
+// kernels.cu -- sm_103a kernels of the shaken-dynamics hot path and their
+// launchers.
+//
+//   k_sweep_bp<HALF>       one half-step over a bit-packed plane (Eq. leftTrans
+//                          for HALF = 0, Eq. rightTrans for HALF = 1) with the
+//                          observable reductions fused
+//   k_sweep_i8<HALF, AL>   the same over an int8 +/-1 plane (AL: L % 32 == 0)
+//   k_cnn<LAYOUT, AL>      nearest-neighbour sum C_nn of a sigma plane
+//   k_init<LAYOUT, AL>     initial states
+//   k_run_small<LAYOUT>    a whole run of n steps inside one CTA, both planes
+//                          held as bits in shared memory (small lattices)
+//
+// Each thread owns 32-site blocks (one bit-packed word); a warp walks 32
+// consecutive blocks together so that the lazy random-plane loop of
+// draw_block() can exit as soon as the whole warp is decided.
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace shk {
+
+struct SweepArgs {
+    const void* src;
+    void* dst;
+    uint32_t L;
+    uint32_t Wr;          // blocks per row (aligned layouts)
+    uint32_t nblocks;     // ceil(N / 32)
+    int64_t N;
+    FastDiv div_row;      // division by Wr
+    uint32_t hs;
+    long long* obs_cur;
+    long long* obs_prev;
+    long long* zero_slot;
+    DrawParams P;
+};
+
+// ------------------------------------------------------------ neighbour gathers
+
+// Bits of block w of a bit-packed (or bit-converted) plane and of the two field
+// neighbours of its sites: HALF 0 -> (x down, x left), HALF 1 -> (x up, x right).
+template <int HALF>
+__device__ __forceinline__ void words_aligned(const uint32_t* __restrict__ pl, uint32_t w,
+                                              uint32_t row, uint32_t col, uint32_t L, uint32_t Wr,
+                                              uint32_t nblocks, uint32_t& S, uint32_t& N1,
+                                              uint32_t& N2) {
+    S = pl[w];
+    if (HALF == 0) {
+        N1 = pl[row > 0 ? w - Wr : w + nblocks - Wr];
+        const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
+        N2 = (S << 1) | (prev >> 31);
+    } else {
+        N1 = pl[row + 1 < L ? w + Wr : w + Wr - nblocks];
+        const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
+        N2 = (S >> 1) | (next << 31);
+    }
+}
+
+__device__ __forceinline__ uint32_t bit_of(const uint32_t* pl, int64_t v) {
+    return (pl[v >> 5] >> (v & 31)) & 1u;
+}
+
+// Generic side length (L % 32 != 0): site-by-site neighbour bits of block w of
+// a bit plane with linear site order.
+template <int HALF>
+__device__ __forceinline__ void words_generic(const uint32_t* pl, uint32_t w, int64_t L, int64_t N,
+                                              uint32_t& S, uint32_t& N1, uint32_t& N2,
+                                              uint32_t& valid) {
+    S = N1 = N2 = valid = 0;
+    for (int p = 0; p < 32; ++p) {
+        const int64_t u = 32 * (int64_t)w + p;
+        if (u >= N) break;
+        const int64_t j = u / L, i = u - j * L;
+        int64_t a, b;
+        if (HALF == 0) {
+            a = j > 0 ? u - L : u + N - L;
+            b = i > 0 ? u - 1 : u + L - 1;
+        } else {
+            a = j + 1 < L ? u + L : u + L - N;
+            b = i + 1 < L ? u + 1 : u + 1 - L;
+        }
+        S |= bit_of(pl, u) << p;
+        N1 |= bit_of(pl, a) << p;
+        N2 |= bit_of(pl, b) << p;
+        valid |= 1u << p;
+    }
+}
+
+// int8 plane, generic L: site-by-site.
+template <int HALF>
+__device__ __forceinline__ void bytes_generic(const int8_t* __restrict__ pl, uint32_t w, int64_t L,
+                                              int64_t N, uint32_t& S, uint32_t& N1, uint32_t& N2,
+                                              uint32_t& valid) {
+    S = N1 = N2 = valid = 0;
+    for (int p = 0; p < 32; ++p) {
+        const int64_t u = 32 * (int64_t)w + p;
+        if (u >= N) break;
+        const int64_t j = u / L, i = u - j * L;
+        int64_t a, b;
+        if (HALF == 0) {
+            a = j > 0 ? u - L : u + N - L;
+            b = i > 0 ? u - 1 : u + L - 1;
+        } else {
+            a = j + 1 < L ? u + L : u + L - N;
+            b = i + 1 < L ? u + 1 : u + 1 - L;
+        }
+        S |= (uint32_t)(pl[u] > 0) << p;
+        N1 |= (uint32_t)(pl[a] > 0) << p;
+        N2 |= (uint32_t)(pl[b] > 0) << p;
+        valid |= 1u << p;
+    }
+}
+
+// int8 plane with L % 32 == 0: two 16-byte loads per 32 sites.
+template <int HALF>
+__device__ __forceinline__ void bytes_aligned(const int8_t* __restrict__ pl, uint32_t w, uint32_t row,
+                                              uint32_t col, uint32_t L, uint32_t Wr,
+                                              uint32_t nblocks, uint32_t& S, uint32_t& N1,
+                                              uint32_t& N2) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(pl + 32 * (size_t)w);
+    S = pack_up32(__ldg(s4), __ldg(s4 + 1));
+    uint32_t wn;
+    if (HALF == 0) wn = row > 0 ? w - Wr : w + nblocks - Wr;
+    else wn = row + 1 < L ? w + Wr : w + Wr - nblocks;
+    const uint4* n4 = reinterpret_cast<const uint4*>(pl + 32 * (size_t)wn);
+    N1 = pack_up32(__ldg(n4), __ldg(n4 + 1));
+    if (HALF == 0) {
+        const size_t idx = col > 0 ? 32 * (size_t)w - 1 : 32 * (size_t)w + L - 1;
+        N2 = (S << 1) | (uint32_t)(__ldg(pl + idx) > 0);
+    } else {
+        const size_t idx = col + 1 < Wr ? 32 * (size_t)w + 32 : 32 * (size_t)w + 32 - L;
+        N2 = (S >> 1) | ((uint32_t)(__ldg(pl + idx) > 0) << 31);
+    }
+}
+
+// ------------------------------------------------------------ half-step sweeps
+
+template <int HALF>
+__device__ __forceinline__ void accumulate_step(int (&acc)[3], uint32_t up, uint32_t S, uint32_t N1,
+                                                uint32_t N2, uint32_t valid, bool cnn) {
+    const int nv = __popc(valid);
+    if (HALF == 0) {
+        acc[0] += 2 * __popc(up) - nv;                                              // M_tau
+        if (cnn) acc[1] += 2 * nv - 2 * (__popc((S ^ N1) & valid) + __popc((S ^ N2) & valid));
+    } else {
+        acc[0] += 2 * __popc(up) - nv;                                              // M_sigma
+        acc[1] += nv - 2 * __popc((up ^ S) & valid);                                // S_q
+        acc[2] += 2 * nv - 2 * (__popc((up ^ N1) & valid) + __popc((up ^ N2) & valid));  // S_J
+    }
+}
+
+template <int HALF>
+__device__ __forceinline__ void finish_step(const int (&acc)[3], const SweepArgs& a) {
+    if (HALF == 0) {
+        const int v[2] = {acc[0], acc[1]};
+        long long* const d[2] = {a.obs_cur ? a.obs_cur + 1 : nullptr,
+                                 a.obs_prev ? a.obs_prev + 4 : nullptr};
+        block_accumulate<2>(v, d);
+    } else {
+        const int v[3] = {acc[0], acc[1], acc[2]};
+        long long* const d[3] = {a.obs_cur ? a.obs_cur + 0 : nullptr,
+                                 a.obs_cur ? a.obs_cur + 2 : nullptr,
+                                 a.obs_cur ? a.obs_cur + 3 : nullptr};
+        block_accumulate<3>(v, d);
+    }
+}
+
+template <int HALF>
+__global__ void __launch_bounds__(256) k_sweep_bp(const SweepArgs a) {
+    const uint32_t* __restrict__ src = static_cast<const uint32_t*>(a.src);
+    uint32_t* __restrict__ dst = static_cast<uint32_t*>(a.dst);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    // nblocks is a multiple of 32 for bit-packed planes: every lane is active.
+    for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
+        const uint32_t w = base + lane;
+        const uint32_t row = fdiv(w, a.div_row);
+        const uint32_t col = w - row * a.Wr;
+        uint32_t S, N1, N2;
+        words_aligned<HALF>(src, w, row, col, a.L, a.Wr, a.nblocks, S, N1, N2);
+        const uint32_t up = draw_block(S, N1, N2, w, 0xffffffffu, a.hs, a.P);
+        dst[w] = up;
+        accumulate_step<HALF>(acc, up, S, N1, N2, 0xffffffffu, cnn);
+    }
+    finish_step<HALF>(acc, a);
+}
+
+template <int HALF, bool ALIGNED>
+__global__ void __launch_bounds__(256) k_sweep_i8(const SweepArgs a) {
+    const int8_t* __restrict__ src = static_cast<const int8_t*>(a.src);
+    int8_t* __restrict__ dst = static_cast<int8_t*>(a.dst);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
+        const uint32_t w = base + lane;
+        const bool active = w < a.nblocks;
+        uint32_t S = 0, N1 = 0, N2 = 0, valid = 0;
+        if (active) {
+            if (ALIGNED) {
+                const uint32_t row = fdiv(w, a.div_row);
+                const uint32_t col = w - row * a.Wr;
+                bytes_aligned<HALF>(src, w, row, col, a.L, a.Wr, a.nblocks, S, N1, N2);
+                valid = 0xffffffffu;
+            } else {
+                bytes_generic<HALF>(src, w, a.L, a.N, S, N1, N2, valid);
+            }
+        }
+        const uint32_t up = draw_block(S, N1, N2, w, valid, a.hs, a.P);
+        if (active) {
+            if (ALIGNED) {
+                uint4 lo, hi;
+                unpack32(up, lo, hi);
+                uint4* d4 = reinterpret_cast<uint4*>(dst + 32 * (size_t)w);
+                d4[0] = lo;
+                d4[1] = hi;
+            } else {
+                for (int p = 0; p < 32; ++p)
+                    if ((valid >> p) & 1u) dst[32 * (int64_t)w + p] = ((up >> p) & 1u) ? 1 : -1;
+            }
+        }
+        accumulate_step<HALF>(acc, up, S, N1, N2, valid, cnn);
+    }
+    finish_step<HALF>(acc, a);
+}
+
+// C_nn = sum sigma_x (sigma_{x down} + sigma_{x left}), equal by translation on
+// the torus to sum sigma_x (sigma_{x up} + sigma_{x right}); added to obs_cur[4].
+template <int LAYOUT, bool ALIGNED>
+__global__ void __launch_bounds__(256) k_cnn(const SweepArgs a) {
+    int acc = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
+        uint32_t S, N1, N2, valid = 0xffffffffu;
+        if (LAYOUT == kBitpack) {
+            const uint32_t row = fdiv(w, a.div_row);
+            words_aligned<0>(static_cast<const uint32_t*>(a.src), w, row, w - row * a.Wr, a.L, a.Wr,
+                             a.nblocks, S, N1, N2);
+        } else if (ALIGNED) {
+            const uint32_t row = fdiv(w, a.div_row);
+            bytes_aligned<0>(static_cast<const int8_t*>(a.src), w, row, w - row * a.Wr, a.L, a.Wr,
+                             a.nblocks, S, N1, N2);
+        } else {
+            bytes_generic<0>(static_cast<const int8_t*>(a.src), w, a.L, a.N, S, N1, N2, valid);
+        }
+        const int nv = __popc(valid);
+        acc += 2 * nv - 2 * (__popc((S ^ N1) & valid) + __popc((S ^ N2) & valid));
+    }
+    const int v[1] = {acc};
+    long long* const d[1] = {a.obs_cur ? a.obs_cur + 4 : nullptr};
+    block_accumulate<1>(v, d);
+}
+
+// ------------------------------------------------------------ initial states
+
+struct InitArgs {
+    void* plane;
+    uint32_t L;
+    uint32_t nblocks;
+    int64_t N;
+    int kind;
+    uint32_t plane_index;
+    DrawParams P;   // only the round keys, lattice id and c3_base are used
+};
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(256) k_init(const InitArgs a) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
+        uint32_t bits;
+        if (a.kind == 0) {
+            bits = 0xffffffffu;
+        } else if (a.kind == 1) {
+            bits = 0u;
+        } else {
+            // r(u) < 2^31 iff the most significant bit of r(u) is 0, i.e. bit
+            // p of the first Philox word of the block is 0.
+            uint32_t x0 = a.plane_index, x1 = w, x2 = a.P.lattice_id, x3 = a.P.c3_base;
+            philox10(x0, x1, x2, x3, a.P);
+            bits = ~x0;
+        }
+        const int64_t rem = a.N - 32 * (int64_t)w;
+        const uint32_t valid = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        bits &= valid;
+        if (LAYOUT == kBitpack) {
+            static_cast<uint32_t*>(a.plane)[w] = bits;
+        } else if (valid == 0xffffffffu && ((a.L & 31u) == 0u)) {
+            uint4 lo, hi;
+            unpack32(bits, lo, hi);
+            uint4* d4 = reinterpret_cast<uint4*>(static_cast<int8_t*>(a.plane) + 32 * (size_t)w);
+            d4[0] = lo;
+            d4[1] = hi;
+        } else {
+            int8_t* d = static_cast<int8_t*>(a.plane);
+            for (int p = 0; p < 32; ++p)
+                if ((valid >> p) & 1u) d[32 * (int64_t)w + p] = ((bits >> p) & 1u) ? 1 : -1;
+        }
+    }
+}
+
+// ------------------------------------------------------------ small lattices
+
+struct SmallArgs {
+    void* sigma;
+    void* tau;
+    uint32_t L;
+    uint32_t Wr;
+    uint32_t nblocks;
+    uint32_t nbp;       // nblocks rounded up to a multiple of 32
+    int64_t N;
+    int aligned;
+    FastDiv div_row;
+    uint64_t t0;
+    uint32_t n;
+    long long* obs;     // n rows of five sums, nullable
+    long long* last;    // last row, nullable
+    DrawParams P;
+};
+
+template <int HALF>
+__device__ __forceinline__ void small_fields(const uint32_t* pl, uint32_t w, const SmallArgs& a,
+                                             uint32_t& S, uint32_t& N1, uint32_t& N2,
+                                             uint32_t& valid) {
+    if (w >= a.nblocks) {
+        S = N1 = N2 = valid = 0;
+    } else if (a.aligned) {
+        const uint32_t row = fdiv(w, a.div_row);
+        words_aligned<HALF>(pl, w, row, w - row * a.Wr, a.L, a.Wr, a.nblocks, S, N1, N2);
+        valid = 0xffffffffu;
+    } else {
+        words_generic<HALF>(pl, w, a.L, a.N, S, N1, N2, valid);
+    }
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(1024) k_run_small(const SmallArgs a) {
+    extern __shared__ uint32_t sm_planes[];
+    uint32_t* sg = sm_planes;
+    uint32_t* tu = sm_planes + a.nbp;
+    __shared__ long long red[kNumObs][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+
+    // load both planes as bits
+    for (uint32_t w = threadIdx.x; w < a.nbp; w += blockDim.x) {
+        uint32_t bs = 0, bt = 0;
+        if (w < a.nblocks) {
+            if (LAYOUT == kBitpack) {
+                bs = static_cast<const uint32_t*>(a.sigma)[w];
+                bt = static_cast<const uint32_t*>(a.tau)[w];
+            } else {
+                const int8_t* s8 = static_cast<const int8_t*>(a.sigma);
+                const int8_t* t8 = static_cast<const int8_t*>(a.tau);
+                for (int p = 0; p < 32; ++p) {
+                    const int64_t u = 32 * (int64_t)w + p;
+                    if (u >= a.N) break;
+                    bs |= (uint32_t)(s8[u] > 0) << p;
+                    bt |= (uint32_t)(t8[u] > 0) << p;
+                }
+            }
+        }
+        sg[w] = bs;
+        tu[w] = bt;
+    }
+    __syncthreads();
+
+    for (uint32_t s = 0; s < a.n; ++s) {
+        const uint64_t t = a.t0 + s;
+        const uint32_t hs = (uint32_t)(2 * t);
+        for (uint32_t base = warp * 32; base < a.nbp; base += nwarps * 32) {
+            const uint32_t w = base + lane;
+            uint32_t S, N1, N2, valid;
+            small_fields<0>(sg, w, a, S, N1, N2, valid);
+            const uint32_t up = draw_block(S, N1, N2, w, valid, hs, a.P);
+            if (w < a.nblocks) tu[w] = up;
+        }
+        __syncthreads();
+        for (uint32_t base = warp * 32; base < a.nbp; base += nwarps * 32) {
+            const uint32_t w = base + lane;
+            uint32_t S, N1, N2, valid;
+            small_fields<1>(tu, w, a, S, N1, N2, valid);
+            const uint32_t up = draw_block(S, N1, N2, w, valid, hs + 1, a.P);
+            if (w < a.nblocks) sg[w] = up;
+        }
+        __syncthreads();
+        if (a.obs == nullptr && s + 1 < a.n) continue;
+        // observables of (sigma_t, tau_t)
+        int v[kNumObs] = {0, 0, 0, 0, 0};
+        for (uint32_t w = threadIdx.x; w < a.nblocks; w += blockDim.x) {
+            uint32_t Sg, SgU, SgR, Tu, TuU, TuR, valid;
+            small_fields<1>(sg, w, a, Sg, SgU, SgR, valid);
+            small_fields<1>(tu, w, a, Tu, TuU, TuR, valid);
+            const int nv = __popc(valid);
+            v[0] += 2 * __popc(Sg) - nv;
+            v[1] += 2 * __popc(Tu) - nv;
+            v[2] += nv - 2 * __popc((Sg ^ Tu) & valid);
+            v[3] += 2 * nv - 2 * (__popc((Sg ^ TuU) & valid) + __popc((Sg ^ TuR) & valid));
+            v[4] += 2 * nv - 2 * (__popc((Sg ^ SgU) & valid) + __popc((Sg ^ SgR) & valid));
+        }
+#pragma unroll
+        for (int i = 0; i < kNumObs; ++i) {
+            const int r = warp_sum(v[i]);
+            if (lane == 0) red[i][warp] = r;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int i = 0; i < kNumObs; ++i) {
+                long long r = lane < nwarps ? red[i][lane] : 0;
+                r = warp_sum64(r);
+                if (lane == 0) {
+                    if (a.obs) a.obs[(size_t)s * kNumObs + i] = r;
+                    if (s + 1 == a.n && a.last) a.last[i] = r;
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // store both planes back
+    for (uint32_t w = threadIdx.x; w < a.nblocks; w += blockDim.x) {
+        if (LAYOUT == kBitpack) {
+            static_cast<uint32_t*>(a.sigma)[w] = sg[w];
+            static_cast<uint32_t*>(a.tau)[w] = tu[w];
+        } else {
+            int8_t* s8 = static_cast<int8_t*>(a.sigma);
+            int8_t* t8 = static_cast<int8_t*>(a.tau);
+            for (int p = 0; p < 32; ++p) {
+                const int64_t u = 32 * (int64_t)w + p;
+                if (u >= a.N) break;
+                s8[u] = ((sg[w] >> p) & 1u) ? 1 : -1;
+                t8[u] = ((tu[w] >> p) & 1u) ? 1 : -1;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// Resident blocks per SM of a kernel at a block size, queried once per kernel.
+static int blocks_per_sm(const void* kernel, int block) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(kernel);
+    if (it != cache.end()) return it->second;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    if (per_sm <= 0) per_sm = 1;
+    cache.emplace(kernel, per_sm);
+    return per_sm;
+}
+
+// Grid of at most one full wave of resident blocks (the kernels stride over
+// their work), never more blocks than work items need.
+template <class K>
+static int grid_for(K kernel, int block, uint64_t work_items) {
+    const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kernel), block);
+    const uint64_t full = (uint64_t)per_sm * sm_count();
+    const uint64_t need = (work_items + block - 1) / block;
+    return (int)std::max<uint64_t>(1, std::min(full, need));
+}
+
+static SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawParams& P,
+                            uint32_t hs, long long* oc, long long* op, long long* z) {
+    SweepArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.L = (uint32_t)g.L;
+    a.Wr = g.Wr;
+    a.nblocks = g.nblocks;
+    a.N = g.N;
+    a.div_row = make_fastdiv(g.Wr > 0 ? g.Wr : 1);
+    a.hs = hs;
+    a.obs_cur = oc;
+    a.obs_prev = op;
+    a.zero_slot = z;
+    a.P = P;
+    return a;
+}
+
+cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* dst,
+                            const DrawParams& P, uint32_t hs, long long* obs_cur,
+                            long long* obs_prev, long long* zero_slot, cudaStream_t st) {
+    const SweepArgs a = sweep_args(g, src, dst, P, hs, obs_cur, half == 0 ? obs_prev : nullptr,
+                                   zero_slot);
+    const int block = 256;
+    if (g.layout == kBitpack) {
+        if (half == 0) {
+            k_sweep_bp<0><<<grid_for(k_sweep_bp<0>, block, g.nblocks), block, 0, st>>>(a);
+        } else {
+            k_sweep_bp<1><<<grid_for(k_sweep_bp<1>, block, g.nblocks), block, 0, st>>>(a);
+        }
+    } else if (g.aligned) {
+        if (half == 0) {
+            k_sweep_i8<0, true><<<grid_for(k_sweep_i8<0, true>, block, g.nblocks), block, 0, st>>>(a);
+        } else {
+            k_sweep_i8<1, true><<<grid_for(k_sweep_i8<1, true>, block, g.nblocks), block, 0, st>>>(a);
+        }
+    } else {
+        if (half == 0) {
+            k_sweep_i8<0, false><<<grid_for(k_sweep_i8<0, false>, block, g.nblocks), block, 0, st>>>(a);
+        } else {
+            k_sweep_i8<1, false><<<grid_for(k_sweep_i8<1, false>, block, g.nblocks), block, 0, st>>>(a);
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cnn(const Geometry& g, const void* sigma, long long* obs, cudaStream_t st) {
+    DrawParams P{};
+    const SweepArgs a = sweep_args(g, sigma, nullptr, P, 0, obs, nullptr, nullptr);
+    const int block = 256;
+    if (g.layout == kBitpack) {
+        k_cnn<kBitpack, true><<<grid_for(k_cnn<kBitpack, true>, block, g.nblocks), block, 0, st>>>(a);
+    } else if (g.aligned) {
+        k_cnn<kInt8, true><<<grid_for(k_cnn<kInt8, true>, block, g.nblocks), block, 0, st>>>(a);
+    } else {
+        k_cnn<kInt8, false><<<grid_for(k_cnn<kInt8, false>, block, g.nblocks), block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Geometry& g, void* plane, int kind, uint64_t init_seed,
+                        uint32_t lattice_id, uint32_t plane_index, cudaStream_t st) {
+    InitArgs a;
+    a.plane = plane;
+    a.L = (uint32_t)g.L;
+    a.nblocks = g.nblocks;
+    a.N = g.N;
+    a.kind = kind;
+    a.plane_index = plane_index;
+    const uint32_t dummyT[6] = {0x80000000u, 0x80000000u, 0x80000000u,
+                                0x80000000u, 0x80000000u, 0x80000000u};
+    make_draw_params(init_seed, lattice_id, dummyT, 1u, &a.P);
+    const int block = 256;
+    if (g.layout == kBitpack) {
+        k_init<kBitpack><<<grid_for(k_init<kBitpack>, block, g.nblocks), block, 0, st>>>(a);
+    } else {
+        k_init<kInt8><<<grid_for(k_init<kInt8>, block, g.nblocks), block, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+static uint32_t small_block_threads(const Geometry& g) {
+    const uint32_t nbp = (g.nblocks + 31u) & ~31u;
+    return std::min<uint32_t>(1024u, std::max<uint32_t>(32u, nbp));
+}
+
+bool small_path_fits(const Geometry& g) {
+    // Lattices up to 2^16 sites per plane (L <= 256) run faster inside one CTA
+    // than as a sequence of grid-wide launches.
+    return g.N <= 65536;
+}
+
+cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const DrawParams& P,
+                             uint64_t t0, uint64_t n, long long* obs, long long* last,
+                             cudaStream_t st) {
+    SmallArgs a;
+    a.sigma = sigma;
+    a.tau = tau;
+    a.L = (uint32_t)g.L;
+    a.Wr = g.Wr;
+    a.nblocks = g.nblocks;
+    a.nbp = (g.nblocks + 31u) & ~31u;
+    a.N = g.N;
+    a.aligned = g.aligned ? 1 : 0;
+    a.div_row = make_fastdiv(g.Wr > 0 ? g.Wr : 1);
+    a.t0 = t0;
+    a.n = (uint32_t)n;
+    a.obs = obs;
+    a.last = last;
+    a.P = P;
+    const uint32_t threads = small_block_threads(g);
+    const size_t smem = 2 * (size_t)a.nbp * sizeof(uint32_t);
+    if (g.layout == kBitpack) {
+        k_run_small<kBitpack><<<1, threads, smem, st>>>(a);
+    } else {
+        k_run_small<kInt8><<<1, threads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace shk

@@ -1,0 +1,109 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol the header
+declares, computes the same threshold table as the oracle (independently
+written), and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1908_07341_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_1908_07341_gb300 import build
+    build.build()
+    return _lib.lib()
+
+
+def _declared_functions():
+    with open(os.path.join(ROOT, "include", "shaken.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(shk_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(so):
+    names = _declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(so, name), name
+        assert name in _lib.SIGNATURES, f"binding lacks {name}"
+    assert set(_lib.SIGNATURES) <= set(names)
+
+
+def test_header_constants_match_binding():
+    with open(os.path.join(ROOT, "include", "shaken.h")) as f:
+        text = f.read()
+    consts = dict(re.findall(r"#define\s+(SHK_[A-Z0-9_]+)\s+\(?(-?[0-9x]+)", text))
+    for name, val in (("SHK_OK", _lib.OK), ("SHK_EINVAL", _lib.EINVAL), ("SHK_ESTATE", _lib.ESTATE),
+                      ("SHK_BITPACK", _lib.BITPACK), ("SHK_INT8", _lib.INT8),
+                      ("SHK_INIT_RANDOM", _lib.INIT_RANDOM), ("SHK_NOBS", _lib.NOBS),
+                      ("SHK_MAX_L", _lib.MAX_L)):
+        assert int(consts[name], 0) == val, name
+
+
+@pytest.mark.parametrize("q,J", [(1.0, 0.25), (0.5, 0.5), (1.0, 0.35), (0.6585, 0.6585),
+                                 (3.0, 0.44), (0.0, 0.0), (-2.0, 0.7), (30.0, 30.0), (1e-12, 0.0)])
+def test_thresholds_equal_the_oracle(so, orc, q, J):
+    out = np.zeros(6, dtype=np.uint32)
+    assert so.shk_thresholds(q, J, out.ctypes.data) == _lib.OK
+    assert np.array_equal(out, orc.thresholds(q, J))
+
+
+def test_thresholds_equal_the_oracle_on_a_grid(so, orc):
+    rng = np.random.default_rng(0)
+    out = np.zeros(6, dtype=np.uint32)
+    for q, J in rng.uniform(-4, 4, size=(2000, 2)):
+        so.shk_thresholds(q, J, out.ctypes.data)
+        assert np.array_equal(out, orc.thresholds(q, J))
+
+
+def test_bad_arguments_are_rejected_without_a_gpu(so):
+    out = np.zeros(6, dtype=np.uint32)
+    assert so.shk_thresholds(float("nan"), 0.1, out.ctypes.data) == _lib.EINVAL
+    assert b"finite" in so.shk_last_error(None)
+    assert so.shk_plane_bytes(33, _lib.BITPACK) == 0
+    assert so.shk_plane_bytes(1, _lib.INT8) == 0
+    assert so.shk_plane_bytes(_lib.MAX_L * 2, _lib.INT8) == 0
+    assert so.shk_plane_bytes(64, 7) == 0
+    assert so.shk_plane_bytes(64, _lib.BITPACK) == 512
+    assert so.shk_lattice_bytes(16384, _lib.BITPACK) == 2 * 16384 * 16384 // 8 + 256
+    h = ctypes.c_void_p()
+    assert so.shk_lattice_create(33, _lib.BITPACK, 256, 1 << 20, None, ctypes.byref(h)) == _lib.EINVAL
+    assert so.shk_lattice_create(64, _lib.BITPACK, 0, 1 << 20, None, ctypes.byref(h)) == _lib.EINVAL
+    assert so.shk_lattice_create(64, _lib.BITPACK, 100, 1 << 20, None, ctypes.byref(h)) == _lib.EINVAL
+    assert so.shk_lattice_create(64, _lib.BITPACK, 256, 16, None, ctypes.byref(h)) == _lib.ENOMEM
+    assert b"needed" in so.shk_last_error(None)
+    bad_T = np.full(6, 7, dtype=np.uint32)
+    assert so.shk_halfstep(_lib.BITPACK, 0, 256, 512, 64, bad_T.ctypes.data, 1, 0, 0, None,
+                           None) == _lib.EINVAL
+    assert so.shk_halfstep(_lib.BITPACK, 2, 256, 512, 64, out.ctypes.data, 1, 0, 0, None,
+                           None) == _lib.EINVAL
+    assert so.shk_run(None, 5, None) == _lib.EINVAL
+    assert so.shk_strerror(_lib.EBUSY) == b"busy"
+
+
+def test_handle_state_checks_without_a_gpu(so):
+    # A handle over a fake (never dereferenced) aligned address: configuration
+    # calls are host-only, and running before set_params is refused.
+    h = ctypes.c_void_p()
+    need = so.shk_lattice_bytes(64, _lib.BITPACK)
+    assert so.shk_lattice_create(64, _lib.BITPACK, 1 << 20, need, None, ctypes.byref(h)) == _lib.OK
+    try:
+        assert so.shk_run(h, 3, None) == _lib.ESTATE
+        assert b"set_params" in so.shk_last_error(h)
+        assert so.shk_set_params(h, float("inf"), 0.2) == _lib.EINVAL
+        assert so.shk_set_step(h, _lib.MAX_STEP) == _lib.EINVAL
+        assert so.shk_set_step(h, 41) == _lib.OK
+        t = ctypes.c_uint64()
+        assert so.shk_get_step(h, ctypes.byref(t)) == _lib.OK and t.value == 41
+        out = np.zeros(5, dtype=np.int64)
+        assert so.shk_read_observables(h, out.ctypes.data) == _lib.ESTATE
+        assert so.shk_plane_ptr(h, 1) == (1 << 20) + 512
+    finally:
+        so.shk_lattice_destroy(h)
