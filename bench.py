@@ -80,7 +80,7 @@ def _expected_algorithmic_ops_per_block():
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons during the timed region."""
 
-    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
 
@@ -94,12 +94,14 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """Stops sampling; keeps the samples whose timestamp falls inside
+        window = (t0, t1) in time.time() seconds (all samples if none do)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -108,7 +110,8 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -116,17 +119,18 @@ class ClockSampler:
                 if len(parts) < len(self.FIELDS):
                     continue
                 try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[1]), float(parts[2]),
+                                 [n for n, v in zip(names, parts[5:9]) if v.lower() == "active"]))
                 except ValueError:
                     continue
-                for name, val in zip(names, parts[5:9]):
-                    if val.lower() == "active":
-                        reasons.add(name)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        inside = [r for r in rows if window and window[0] - 0.05 <= r[0] <= window[1] + 0.05]
+        use = inside or rows
+        reasons = sorted({n for r in use for n in r[3]})
+        return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+                "sm_max_mhz": max(r[2] for r in use) if use else None,
+                "samples": len(use), "in_timed_window": bool(inside), "reasons": reasons}
 
 
 # ----------------------------------------------------------------- oracle timing
@@ -214,6 +218,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream(dev)
+    window = [0.0, 0.0]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def bench_layout(layout: str, steps: int, warmup: int, with_e2e: bool):
@@ -228,12 +233,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         barrier()
+        window[0] = time.time()
         for k in range(steps):
             flush.fill_(k & 0xFF)               # evict L2 between timed steps (not timed)
             starts[k].record(stream)
             lat.run(STEPS_PER_BENCH_STEP, obs)
             ends[k].record(stream)
         barrier()
+        window[1] = time.time()
         ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
         e2e = None
         if with_e2e:
@@ -284,10 +291,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sampler = ClockSampler(local_rank) if rank == 0 else None
     if sampler:
         sampler.start()
+        time.sleep(0.3)                          # nvidia-smi start-up
     t_wall0 = time.perf_counter()
     ms, e2e, kern_ms = bench_layout("bitpack", args.steps, args.warmup, with_e2e=True)
     wall = time.perf_counter() - t_wall0
-    clocks = sampler.stop() if sampler else None
+    clocks = sampler.stop(tuple(window)) if sampler else None
 
     def max_over_ranks(x: float) -> float:
         if dist is None:
