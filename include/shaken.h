@@ -209,6 +209,40 @@ int shk_download_plane(shk_lattice* lat, int plane, void* host_raw, size_t bytes
 /* Device pointer of plane 0 (sigma) or 1 (tau) inside the handle's memory. */
 void* shk_plane_ptr(shk_lattice* lat, int plane);
 
+/* ------------------------------------------------------------ allocation-free run */
+
+/* Largest tau plane the library's own scratch array holds (8 MiB): bit-packed
+ * L <= 8192, int8 L <= 2896. */
+#define SHK_STATIC_SCRATCH_PLANE_BYTES (8u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory.  Examples are a plug-in inside a host
+ * application that owns all device memory through its own pool, or a
+ * latency-critical loop in which cudaMalloc's implicit synchronisation is not
+ * acceptable.  It runs n_steps full steps t0 .. t0+n_steps-1 of the shaken
+ * chain (the sigma-marginal of the alternate dynamics) in place on the
+ * caller's sigma plane, and gives the same spins and sums as shk_run on a
+ * handle holding that sigma.
+ *   sigma     device plane of shk_plane_bytes(L, layout) bytes (input and output).
+ *   last_obs  nullable device array of SHK_NOBS int64: the five sums of the
+ *             last step (sigma, tau at its end).
+ *   stream    cudaStream_t as void*; the device that is current at the call
+ *             is the one used.
+ * The call allocates nothing and calls no allocating routine.  The transient
+ * tau plane and the observable accumulators live in a file-scope static device
+ * array of 8 MiB + 256 B.  Every GPU that loads the library holds that array
+ * until the process exits.  The array keeps the last call's contents;
+ * accumulators are cleared at the start of every call.  Calls whose GPU work
+ * overlaps (different streams or host threads) share the array and race.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Errors: SHK_EINVAL for sizes beyond the scratch (message says the limit),
+ * bad L/layout, non-finite q or J, or a step index reaching SHK_MAX_STEP;
+ * SHK_ECUDA if a launch fails.  Messages via shk_last_error(NULL). */
+int shk_shaken_run_static(int layout, void* sigma, int L, double q, double J, uint64_t seed,
+                          uint32_t lattice_id, uint64_t t0, uint64_t n_steps, int64_t* last_obs,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,7 @@ SIGNATURES = {
     "shk_upload_plane": (_i, [_vp, _i, _vp, _sz]),
     "shk_download_plane": (_i, [_vp, _i, _vp, _sz]),
     "shk_plane_ptr": (_vp, [_vp, _i]),
+    "shk_shaken_run_static": (_i, [_i, _vp, _i, _d, _d, _u64, _u32, _u64, _u64, _vp, _vp]),
 }
 
 

@@ -132,6 +132,8 @@ constexpr size_t kRingBytes = 256;
 
 }  // namespace
 
+void shk::set_thread_error(const char* msg) { g_thread_err = msg ? msg : ""; }
+
 extern "C" {
 
 const char* shk_strerror(int status) {

@@ -60,4 +60,7 @@ cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const Dr
 // Number of SMs of the current device (cached).
 int sm_count();
 
+// Message returned by shk_last_error(NULL) on this host thread.
+void set_thread_error(const char* msg);
+
 }  // namespace shk
