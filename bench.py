@@ -372,15 +372,55 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     return 0
 
 
+def run_kernel_case(spec: str) -> int:
+    """--kernel-case LAYOUT:L:LAUNCHES -- a random-start lattice and LAUNCHES
+    alternating half-step launches through shk_halfstep (the benchmark's
+    kernel and grid), nothing else: the command profiled in profiles/."""
+    import torch
+
+    from paper_1908_07341_gb300 import build as libbuild
+
+    libbuild.build()
+    import paper_1908_07341_gb300 as shk
+
+    layout, side, launches = spec.split(":")
+    side, launches = int(side), int(launches)
+    lat = shk.Lattice(side, layout).set_seed(SEED, 0).set_params(Q, J).init("random", init_seed=INIT_SEED)
+    T = shk.thresholds(Q, J)
+    acc = torch.zeros(shk.NOBS, dtype=torch.int64, device="cuda")
+    a, b = lat.plane(0), lat.plane(1)
+    for k in range(launches):
+        half = k & 1
+        shk.halfstep(layout, half, a if half == 0 else b, b if half == 0 else a, side, T, SEED, 0, k, acc)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": spec, "sums": acc.cpu().tolist()}))
+    return 0
+
+
+def _kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("device.cuh", "kernels.cu"):
+        with open(os.path.join(ROOT, "paper_1908_07341_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def _load_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if present and
-    taken on the current kernels (see profiles/)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu summaries (profiles/
+    traffic.txt), kept only when they were taken on the current kernel sources."""
+    out = {}
     try:
-        with open(path) as f:
-            return json.load(f)
+        current = _kernel_source_hash()
+        with open(os.path.join(ROOT, "profiles", "traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and not line.startswith("#") and parts[2] == current:
+                    out[parts[0]] = int(parts[1])
     except Exception:
         return {}
+    return out
 
 
 def main():
@@ -390,7 +430,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", default=None,
+                    help="LAYOUT:L:LAUNCHES -- only run half-step launches (for profiling)")
     args = ap.parse_args()
+    if args.kernel_case:
+        return run_kernel_case(args.kernel_case)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     world = int(os.environ.get("WORLD_SIZE", "1"))
