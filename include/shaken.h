@@ -142,6 +142,20 @@ int shk_halfstep(int layout, int half, const void* src, void* dst, int L,
                  const uint32_t T[6], uint64_t seed, uint32_t lattice_id,
                  uint32_t hs, int64_t* obs_accum, void* stream);
 
+/* Launch-shape variants of the half-step sweep kernels (bit-packed, and int8
+ * with L % 32 == 0): blocks drawn per thread, load prefetching, block size and
+ * resident blocks per SM.  The choice does not change any result -- every
+ * variant draws the same spins -- only the speed.  The setting is
+ * process-wide and applies to launches enqueued after the call; the autotuner
+ * (paper_1908_07341_gb300.tune) times the variants and sets the fastest.
+ * The paper has no counterpart (it is a property of this implementation).
+ * shk_sweep_variant_name returns NULL for an unknown (layout, variant);
+ * shk_set_sweep_variant returns SHK_EINVAL for one. */
+int shk_sweep_variant_count(int layout);
+const char* shk_sweep_variant_name(int layout, int variant);
+int shk_get_sweep_variant(int layout);
+int shk_set_sweep_variant(int layout, int variant);
+
 /* Fills a device plane with an initial state: all +1, all -1 or random
  * (+1 iff the site uniform of counter (plane_index, u >> 5, lattice_id,
  * 256 + c) under key init_seed is below 2^31).  Asynchronous. */

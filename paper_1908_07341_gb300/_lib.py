@@ -34,6 +34,10 @@ SIGNATURES = {
     "shk_thresholds": (_i, [_d, _d, _vp]),
     "shk_plane_bytes": (_sz, [_i, _i]),
     "shk_halfstep": (_i, [_i, _i, _vp, _vp, _i, _vp, _u64, _u32, _u32, _vp, _vp]),
+    "shk_sweep_variant_count": (_i, [_i]),
+    "shk_sweep_variant_name": (_c.c_char_p, [_i, _i]),
+    "shk_get_sweep_variant": (_i, [_i]),
+    "shk_set_sweep_variant": (_i, [_i, _i]),
     "shk_init_plane": (_i, [_i, _vp, _i, _i, _u64, _u32, _u32, _vp]),
     "shk_lattice_bytes": (_sz, [_i, _i]),
     "shk_lattice_create": (_i, [_i, _i, _vp, _sz, _vp, _vp]),

@@ -188,6 +188,22 @@ int shk_halfstep(int layout, int half, const void* src, void* dst, int L, const 
     return SHK_OK;
 }
 
+int shk_sweep_variant_count(int layout) { return sweep_variant_count(layout); }
+
+const char* shk_sweep_variant_name(int layout, int variant) { return sweep_variant_name(layout, variant); }
+
+int shk_get_sweep_variant(int layout) {
+    if (sweep_variant_count(layout) == 0)
+        return fail(nullptr, SHK_EINVAL, "shk_get_sweep_variant: unknown layout %d", layout);
+    return get_sweep_variant(layout);
+}
+
+int shk_set_sweep_variant(int layout, int variant) {
+    if (!set_sweep_variant(layout, variant))
+        return fail(nullptr, SHK_EINVAL, "shk_set_sweep_variant: no variant %d for layout %d", variant, layout);
+    return SHK_OK;
+}
+
 int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
                    uint32_t lattice_id, uint32_t plane_index, void* stream) {
     Geometry g;

@@ -68,43 +68,145 @@ __device__ __forceinline__ void philox10(uint32_t& c0, uint32_t& c1, uint32_t& c
     }
 }
 
-// Draws the 32 spins of block w (sites 32w .. 32w+31).
+// Draws the 32 spins of each of K blocks w[k] (sites 32w .. 32w+31), with the
+// K Philox chains interleaved for instruction-level parallelism.
 //   S      bits of the sites themselves in the source plane (1 = +1)
 //   A, B   bits of the two field neighbours of each site
 //   valid  sites that exist (bits beyond the plane are 0 and never delay exit)
 //   hs     half-step index (first counter word)
 // All 32 lanes of the warp must call this together: the loop over random
-// planes stops when no lane has an undecided valid site.
-template <class PP>
-__device__ __forceinline__ uint32_t draw_block(uint32_t S, uint32_t A, uint32_t B, uint32_t w,
-                                               uint32_t valid, uint32_t hs, const PP& P) {
-    const uint32_t F = ~S;                 // sites that are -1
-    const uint32_t a1 = ~(A ^ S);          // neighbour A agrees with the site
-    const uint32_t a2 = ~(B ^ S);
-    const uint32_t C2 = a1 & a2;           // both neighbours agree
-    const uint32_t Cg = a1 | a2;           // at least one agrees
-    uint32_t und = valid;                  // not yet decided
-    uint32_t up = 0;                       // decided +1
+// planes stops when no lane has an undecided valid site in any of its blocks.
+template <int K, class PP>
+__device__ __forceinline__ void draw_blocks(const uint32_t (&S)[K], const uint32_t (&A)[K],
+                                            const uint32_t (&B)[K], const uint32_t (&w)[K],
+                                            const uint32_t (&valid)[K], uint32_t hs, const PP& P,
+                                            uint32_t (&up)[K]) {
+    uint32_t F[K], C2[K], Cg[K], und[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        F[k] = ~S[k];                       // sites that are -1
+        const uint32_t a1 = ~(A[k] ^ S[k]); // neighbour A agrees with the site
+        const uint32_t a2 = ~(B[k] ^ S[k]);
+        C2[k] = a1 & a2;                    // both neighbours agree
+        Cg[k] = a1 | a2;                    // at least one agrees
+        und[k] = valid[k];                  // not yet decided
+        up[k] = 0;                          // decided +1
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        uint32_t x0 = hs, x1 = w, x2 = P.lattice_id, x3 = P.c3_base + (uint32_t)c;
-        philox10(x0, x1, x2, x3, P);
-        const uint32_t R[4] = {x0, x1, x2, x3};
+        uint32_t R[K][4];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            uint32_t x0 = hs, x1 = w[k], x2 = P.lattice_id, x3 = P.c3_base + (uint32_t)c;
+            philox10(x0, x1, x2, x3, P);
+            R[k][0] = x0;
+            R[k][1] = x1;
+            R[k][2] = x2;
+            R[k][3] = x3;
+        }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int b = 4 * c + m;
-            const uint32_t x = R[m];
-            // g: the raw random bit value that would decide the site as +1,
-            // i.e. the class threshold bit, complemented for - sites.
-            const uint32_t g = F ^ P.m0[b] ^ (Cg & P.d01[b]) ^ (C2 & P.d12[b]);
-            up |= und & ~x & g;
-            und &= ~(x ^ g);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const uint32_t x = R[k][m];
+                // g: the raw random bit value that would decide the site as +1,
+                // i.e. the class threshold bit, complemented for - sites.
+                const uint32_t g = F[k] ^ P.m0[b] ^ (Cg[k] & P.d01[b]) ^ (C2[k] & P.d12[b]);
+                up[k] |= und[k] & ~x & g;
+                und[k] &= ~(x ^ g);
+            }
         }
-        if (c < 7 && !__any_sync(0xffffffffu, und != 0u)) break;
+        if (c < 7) {
+            uint32_t any = 0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) any |= und[k];
+            if (!__any_sync(0xffffffffu, any != 0u)) break;
+        }
     }
-    // A uniform equal to its threshold is not below it: + sites stay -1 ... and
-    // - sites (compared through the complement) come out +1.
-    return up | (und & F);
+    // A uniform equal to its threshold is not below it.  A + site therefore
+    // stays -1; a - site compares its complemented uniform, so it comes out +1.
+#pragma unroll
+    for (int k = 0; k < K; ++k) up[k] |= und[k] & F[k];
+}
+
+// ---------------------------------------------------------------- two-phase draw
+//
+// Two Philox calls (8 planes) settle a 32-site block with probability
+// (1 - 2^-8)^32 = 0.88, but a warp that runs the lazy loop to the end waits
+// for the slowest of its 32 blocks and so needs 3.2 calls per block on
+// average.  The two-phase form runs calls 0 and 1 unconditionally (two
+// independent Philox chains), parks the blocks that still have undecided
+// sites in a warp-private queue, and continues 32 parked blocks at a time
+// from call 2 with the lazy early exit.  The result is the same comparison,
+// bit for bit.
+
+// Class masks of a block (see draw_blocks).
+struct BlockClass {
+    uint32_t F, Cg, C2;
+};
+
+__device__ __forceinline__ BlockClass block_class(uint32_t S, uint32_t A, uint32_t B) {
+    const uint32_t a1 = ~(A ^ S), a2 = ~(B ^ S);
+    return {~S, a1 | a2, a1 & a2};
+}
+
+// Philox call c of block w in half-step hs: random planes 4c .. 4c+3.
+template <class PP>
+__device__ __forceinline__ uint4 philox_call(uint32_t w, uint32_t hs, int c, const PP& P) {
+    uint32_t x0 = hs, x1 = w, x2 = P.lattice_id, x3 = P.c3_base + (uint32_t)c;
+    philox10(x0, x1, x2, x3, P);
+    return make_uint4(x0, x1, x2, x3);
+}
+
+// Applies the four planes of call c to the state (und, up) of one block.
+template <class PP>
+__device__ __forceinline__ void apply_planes(const uint4& R, int c, const BlockClass& k, uint32_t& und,
+                                             uint32_t& up, const PP& P) {
+    const uint32_t x[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int b = 4 * c + m;
+        const uint32_t g = k.F ^ P.m0[b] ^ (k.Cg & P.d01[b]) ^ (k.C2 & P.d12[b]);
+        up |= und & ~x[m] & g;
+        und &= ~(x[m] ^ g);
+    }
+}
+
+// Phase 1: calls 0 and 1 for one block.
+template <class PP>
+__device__ __forceinline__ void draw_first_two(const BlockClass& k, uint32_t w, uint32_t valid,
+                                               uint32_t hs, const PP& P, uint32_t& und,
+                                               uint32_t& up) {
+    const uint4 R0 = philox_call(w, hs, 0, P);
+    const uint4 R1 = philox_call(w, hs, 1, P);
+    und = valid;
+    up = 0;
+    apply_planes(R0, 0, k, und, up, P);
+    apply_planes(R1, 1, k, und, up, P);
+}
+
+// Phase 2: calls 2..7 with the lazy exit; all 32 lanes call it together.
+template <class PP>
+__device__ __forceinline__ uint32_t draw_rest(const BlockClass& k, uint32_t w, uint32_t und,
+                                              uint32_t up, uint32_t hs, const PP& P) {
+#pragma unroll
+    for (int c = 2; c < 8; ++c) {
+        if (!__any_sync(0xffffffffu, und != 0u)) break;
+        const uint4 R = philox_call(w, hs, c, P);
+        apply_planes(R, c, k, und, up, P);
+    }
+    return up | (und & k.F);
+}
+
+// One block (the common case).
+template <class PP>
+__device__ __forceinline__ uint32_t draw_block(uint32_t S, uint32_t A, uint32_t B, uint32_t w,
+                                               uint32_t valid, uint32_t hs, const PP& P) {
+    const uint32_t s1[1] = {S}, a1[1] = {A}, b1[1] = {B}, w1[1] = {w}, v1[1] = {valid};
+    uint32_t up[1];
+    draw_blocks<1>(s1, a1, b1, w1, v1, hs, P, up);
+    return up[0];
 }
 
 // ---------------------------------------------------------------- int8 <-> bits

@@ -43,6 +43,13 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
                             const DrawParams& P, uint32_t hs, long long* obs_cur,
                             long long* obs_prev, long long* zero_slot, cudaStream_t st);
 
+// Launch-shape variants of the half-step sweeps (per layout; the int8 table
+// applies to L % 32 == 0).  The choice is process-wide.
+int sweep_variant_count(int layout);
+const char* sweep_variant_name(int layout, int v);
+int get_sweep_variant(int layout);
+bool set_sweep_variant(int layout, int v);
+
 // C_nn of a sigma plane added to obs[4].
 cudaError_t launch_cnn(const Geometry& g, const void* sigma, long long* obs, cudaStream_t st);
 

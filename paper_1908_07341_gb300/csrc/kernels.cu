@@ -1,10 +1,11 @@
 // kernels.cu -- sm_103a kernels of the shaken-dynamics hot path and their
 // launchers.
 //
-//   k_sweep_bp<HALF>       one half-step over a bit-packed plane (Eq. leftTrans
+//   k_sweep_bp<HALF, ...>  one half-step over a bit-packed plane (Eq. leftTrans
 //                          for HALF = 0, Eq. rightTrans for HALF = 1) with the
-//                          observable reductions fused
-//   k_sweep_i8<HALF, AL>   the same over an int8 +/-1 plane (AL: L % 32 == 0)
+//                          observable reductions fused; launch-shape variants
+//   k_sweep_i8a<HALF, ...> the same over an int8 +/-1 plane with L % 32 == 0
+//   k_sweep_i8g<HALF>      the same for any L (site-by-site gathers)
 //   k_cnn<LAYOUT, AL>      nearest-neighbour sum C_nn of a sigma plane
 //   k_init<LAYOUT, AL>     initial states
 //   k_run_small<LAYOUT>    a whole run of n steps inside one CTA, both planes
@@ -14,6 +15,7 @@
 // consecutive blocks together so that the lazy random-plane loop of
 // draw_block() can exit as soon as the whole warp is decided.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 #include <unordered_map>
@@ -167,32 +169,259 @@ __device__ __forceinline__ void finish_step(const int (&acc)[3], const SweepArgs
     }
 }
 
+// Raw words of one bit-packed block as loaded: the block itself, its row
+// neighbour (down for A, up for B) and the adjacent word that supplies the
+// wrap-around bit of the left (A) or right (B) neighbour.
+struct RawBp {
+    uint32_t s, n, x;
+};
+
 template <int HALF>
-__global__ void __launch_bounds__(256) k_sweep_bp(const SweepArgs a) {
+__device__ __forceinline__ RawBp load_bp(const uint32_t* __restrict__ src, uint32_t w,
+                                         const SweepArgs& a) {
+    const uint32_t row = fdiv(w, a.div_row);
+    const uint32_t col = w - row * a.Wr;
+    RawBp r;
+    r.s = __ldg(src + w);
+    if (HALF == 0) {
+        r.n = __ldg(src + (row > 0 ? w - a.Wr : w + a.nblocks - a.Wr));
+        r.x = __ldg(src + (col > 0 ? w - 1 : w + a.Wr - 1));
+    } else {
+        r.n = __ldg(src + (row + 1 < a.L ? w + a.Wr : w + a.Wr - a.nblocks));
+        r.x = __ldg(src + (col + 1 < a.Wr ? w + 1 : w + 1 - a.Wr));
+    }
+    return r;
+}
+
+template <int HALF>
+__device__ __forceinline__ void decode_bp(const RawBp& r, uint32_t& S, uint32_t& N1, uint32_t& N2) {
+    S = r.s;
+    N1 = r.n;
+    N2 = HALF == 0 ? (S << 1) | (r.x >> 31) : (S >> 1) | (r.x << 31);
+}
+
+// Bit-packed half-step.  A warp walks groups of 32 * ILP consecutive blocks;
+// each thread draws ILP blocks with interleaved Philox chains, and, with
+// PREFETCH, issues the loads of its next group before drawing the current one.
+template <int HALF, int ILP, bool PREFETCH, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_bp(const SweepArgs a) {
     const uint32_t* __restrict__ src = static_cast<const uint32_t*>(a.src);
     uint32_t* __restrict__ dst = static_cast<uint32_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32 * ILP;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
     int acc[3] = {0, 0, 0};
-    // nblocks is a multiple of 32 for bit-packed planes: every lane is active.
-    for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
+    // nblocks is a multiple of 32, so a 32-block group is all in or all out and
+    // the validity tests below are uniform across the warp.
+    uint32_t base = gwarp * 32 * ILP;
+    RawBp raw[ILP];
+    if (PREFETCH && base < a.nblocks) {
+#pragma unroll
+        for (int k = 0; k < ILP; ++k)
+            if (base + 32 * k < a.nblocks) raw[k] = load_bp<HALF>(src, base + 32 * k + lane, a);
+    }
+    for (; base < a.nblocks; base += stride) {
+        uint32_t S[ILP], N1[ILP], N2[ILP], w[ILP], valid[ILP], up[ILP];
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            w[k] = base + 32 * k + lane;
+            const bool in = base + 32 * k < a.nblocks;
+            valid[k] = in ? 0xffffffffu : 0u;
+            if (!PREFETCH && in) raw[k] = load_bp<HALF>(src, w[k], a);
+            if (in) decode_bp<HALF>(raw[k], S[k], N1[k], N2[k]);
+            else S[k] = N1[k] = N2[k] = 0;
+        }
+        if (PREFETCH) {
+            const uint32_t nb = base + stride;
+#pragma unroll
+            for (int k = 0; k < ILP; ++k)
+                if (nb + 32 * k < a.nblocks) raw[k] = load_bp<HALF>(src, nb + 32 * k + lane, a);
+        }
+        draw_blocks<ILP>(S, N1, N2, w, valid, a.hs, a.P, up);
+#pragma unroll
+        for (int k = 0; k < ILP; ++k) {
+            if (valid[k]) {
+                dst[w[k]] = up[k];
+                accumulate_step<HALF>(acc, up[k], S[k], N1[k], N2[k], 0xffffffffu, cnn);
+            }
+        }
+    }
+    finish_step<HALF>(acc, a);
+}
+
+// Raw bytes of one int8 block (L % 32 == 0): the 32 sites, the 32 row
+// neighbours and the one byte beyond the block that the left/right field needs.
+struct RawI8 {
+    uint4 s0, s1, n0, n1;
+    int x;
+};
+
+template <int HALF>
+__device__ __forceinline__ RawI8 load_i8(const int8_t* __restrict__ src, uint32_t w, const SweepArgs& a) {
+    const uint32_t row = fdiv(w, a.div_row);
+    const uint32_t col = w - row * a.Wr;
+    RawI8 r;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src + 32 * (size_t)w);
+    r.s0 = __ldg(s4);
+    r.s1 = __ldg(s4 + 1);
+    const uint32_t wn = HALF == 0 ? (row > 0 ? w - a.Wr : w + a.nblocks - a.Wr)
+                                  : (row + 1 < a.L ? w + a.Wr : w + a.Wr - a.nblocks);
+    const uint4* n4 = reinterpret_cast<const uint4*>(src + 32 * (size_t)wn);
+    r.n0 = __ldg(n4);
+    r.n1 = __ldg(n4 + 1);
+    size_t idx;
+    if (HALF == 0) idx = col > 0 ? 32 * (size_t)w - 1 : 32 * (size_t)w + a.L - 1;
+    else idx = col + 1 < a.Wr ? 32 * (size_t)w + 32 : 32 * (size_t)w + 32 - a.L;
+    r.x = __ldg(src + idx);
+    return r;
+}
+
+template <int HALF>
+__device__ __forceinline__ void decode_i8(const RawI8& r, uint32_t& S, uint32_t& N1, uint32_t& N2) {
+    S = pack_up32(r.s0, r.s1);
+    N1 = pack_up32(r.n0, r.n1);
+    N2 = HALF == 0 ? (S << 1) | (uint32_t)(r.x > 0) : (S >> 1) | ((uint32_t)(r.x > 0) << 31);
+}
+
+// int8 half-step for L % 32 == 0 (one 32-byte block per thread per step of
+// the walk, optionally prefetching the next block's bytes).
+template <int HALF, bool PREFETCH, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_i8a(const SweepArgs a) {
+    const int8_t* __restrict__ src = static_cast<const int8_t*>(a.src);
+    int8_t* __restrict__ dst = static_cast<int8_t*>(a.dst);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    uint32_t base = gwarp * 32;
+    RawI8 raw;
+    if (PREFETCH && base < a.nblocks) raw = load_i8<HALF>(src, base + lane, a);
+    for (; base < a.nblocks; base += stride) {
         const uint32_t w = base + lane;
-        const uint32_t row = fdiv(w, a.div_row);
-        const uint32_t col = w - row * a.Wr;
+        if (!PREFETCH) raw = load_i8<HALF>(src, w, a);
         uint32_t S, N1, N2;
-        words_aligned<HALF>(src, w, row, col, a.L, a.Wr, a.nblocks, S, N1, N2);
+        decode_i8<HALF>(raw, S, N1, N2);
+        if (PREFETCH && base + stride < a.nblocks) raw = load_i8<HALF>(src, base + stride + lane, a);
         const uint32_t up = draw_block(S, N1, N2, w, 0xffffffffu, a.hs, a.P);
-        dst[w] = up;
+        uint4 lo, hi;
+        unpack32(up, lo, hi);
+        uint4* d4 = reinterpret_cast<uint4*>(dst + 32 * (size_t)w);
+        d4[0] = lo;
+        d4[1] = hi;
         accumulate_step<HALF>(acc, up, S, N1, N2, 0xffffffffu, cnn);
     }
     finish_step<HALF>(acc, a);
 }
 
-template <int HALF, bool ALIGNED>
-__global__ void __launch_bounds__(256) k_sweep_i8(const SweepArgs a) {
+// ------------------------------------------------------------ two-phase sweeps
+//
+// Each warp owns a ring of kQueueCap parked blocks in shared memory (structure
+// of arrays: block index, undecided mask, decided-up mask and the three input
+// words).  Blocks still undecided after Philox calls 0 and 1 wait there; once
+// 32 are waiting the warp continues them together from call 2 (draw_rest).
+
+constexpr int kQueueCap = 64;   // power of two; at most 31 + 32 entries are held
+constexpr int kQueueFields = 6;
+
+template <int HALF, int LAYOUT>
+__device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uint32_t up, uint32_t S,
+                                             uint32_t N1, uint32_t N2, bool cnn, int (&acc)[3]) {
+    if (LAYOUT == kBitpack) {
+        static_cast<uint32_t*>(a.dst)[w] = up;
+    } else {
+        uint4 lo, hi;
+        unpack32(up, lo, hi);
+        uint4* d4 = reinterpret_cast<uint4*>(static_cast<int8_t*>(a.dst) + 32 * (size_t)w);
+        d4[0] = lo;
+        d4[1] = hi;
+    }
+    accumulate_step<HALF>(acc, up, S, N1, N2, 0xffffffffu, cnn);
+}
+
+// Continues the `count` (<= 32) oldest parked blocks; all lanes call it.
+template <int HALF, int LAYOUT>
+__device__ __forceinline__ void drain_queue(const SweepArgs& a, uint32_t (*q)[kQueueCap], uint32_t head,
+                                            int count, bool cnn, int (&acc)[3]) {
+    const uint32_t lane = threadIdx.x & 31;
+    const bool has = (int)lane < count;
+    const uint32_t i = (head + lane) & (kQueueCap - 1);
+    uint32_t w = 0, und = 0, up = 0, S = 0, N1 = 0, N2 = 0;
+    if (has) {
+        w = q[0][i];
+        und = q[1][i];
+        up = q[2][i];
+        S = q[3][i];
+        N1 = q[4][i];
+        N2 = q[5][i];
+    }
+    const BlockClass k = block_class(S, N1, N2);
+    const uint32_t res = draw_rest(k, w, und, up, a.hs, a.P);
+    if (has) finish_block<HALF, LAYOUT>(a, w, res, S, N1, N2, cnn, acc);
+}
+
+template <int HALF, int LAYOUT, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
+    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
+    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    uint32_t head = 0;
+    int count = 0;
+    const uint32_t below = (1u << lane) - 1u;
+    // nblocks is a multiple of 32 for these layouts: every lane is active.
+    for (uint32_t base = gwarp * 32; base < a.nblocks; base += stride) {
+        const uint32_t w = base + lane;
+        uint32_t S, N1, N2;
+        if (LAYOUT == kBitpack) {
+            const RawBp r = load_bp<HALF>(static_cast<const uint32_t*>(a.src), w, a);
+            decode_bp<HALF>(r, S, N1, N2);
+        } else {
+            const RawI8 r = load_i8<HALF>(static_cast<const int8_t*>(a.src), w, a);
+            decode_i8<HALF>(r, S, N1, N2);
+        }
+        const BlockClass k = block_class(S, N1, N2);
+        uint32_t und, up;
+        draw_first_two(k, w, 0xffffffffu, a.hs, a.P, und, up);
+        const bool parked = und != 0u;
+        const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+        if (parked) {
+            const uint32_t i = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+            q[0][i] = w;
+            q[1][i] = und;
+            q[2][i] = up;
+            q[3][i] = S;
+            q[4][i] = N1;
+            q[5][i] = N2;
+        } else {
+            finish_block<HALF, LAYOUT>(a, w, up, S, N1, N2, cnn, acc);
+        }
+        count += __popc(mask);
+        if (count >= 32) {
+            __syncwarp();
+            drain_queue<HALF, LAYOUT>(a, q, head, 32, cnn, acc);
+            __syncwarp();
+            head = (head + 32) & (kQueueCap - 1);
+            count -= 32;
+        }
+    }
+    if (count > 0) {
+        __syncwarp();
+        drain_queue<HALF, LAYOUT>(a, q, head, count, cnn, acc);
+    }
+    finish_step<HALF>(acc, a);
+}
+
+// int8 half-step for any L (site-by-site neighbour gathers; partial last block).
+template <int HALF>
+__global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {
     const int8_t* __restrict__ src = static_cast<const int8_t*>(a.src);
     int8_t* __restrict__ dst = static_cast<int8_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;
@@ -205,28 +434,11 @@ __global__ void __launch_bounds__(256) k_sweep_i8(const SweepArgs a) {
         const uint32_t w = base + lane;
         const bool active = w < a.nblocks;
         uint32_t S = 0, N1 = 0, N2 = 0, valid = 0;
-        if (active) {
-            if (ALIGNED) {
-                const uint32_t row = fdiv(w, a.div_row);
-                const uint32_t col = w - row * a.Wr;
-                bytes_aligned<HALF>(src, w, row, col, a.L, a.Wr, a.nblocks, S, N1, N2);
-                valid = 0xffffffffu;
-            } else {
-                bytes_generic<HALF>(src, w, a.L, a.N, S, N1, N2, valid);
-            }
-        }
+        if (active) bytes_generic<HALF>(src, w, a.L, a.N, S, N1, N2, valid);
         const uint32_t up = draw_block(S, N1, N2, w, valid, a.hs, a.P);
         if (active) {
-            if (ALIGNED) {
-                uint4 lo, hi;
-                unpack32(up, lo, hi);
-                uint4* d4 = reinterpret_cast<uint4*>(dst + 32 * (size_t)w);
-                d4[0] = lo;
-                d4[1] = hi;
-            } else {
-                for (int p = 0; p < 32; ++p)
-                    if ((valid >> p) & 1u) dst[32 * (int64_t)w + p] = ((up >> p) & 1u) ? 1 : -1;
-            }
+            for (int p = 0; p < 32; ++p)
+                if ((valid >> p) & 1u) dst[32 * (int64_t)w + p] = ((up >> p) & 1u) ? 1 : -1;
         }
         accumulate_step<HALF>(acc, up, S, N1, N2, valid, cnn);
     }
@@ -499,29 +711,80 @@ static SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const
     return a;
 }
 
+// ------------------------------------------------------------ sweep variants
+//
+// Launch shapes of the half-step sweeps, chosen per layout at run time
+// (shk_set_sweep_variant; the autotuner times them and picks one).
+
+using SweepKernel = void (*)(SweepArgs);
+
+struct SweepVariant {
+    SweepKernel k[2];   // half A, half B
+    int block;
+    const char* name;
+};
+
+static const SweepVariant kBpVariants[] = {
+    {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, "queue-256x3"},
+    {{k_sweep_q<0, kBitpack, 256, 4>, k_sweep_q<1, kBitpack, 256, 4>}, 256, "queue-256x4"},
+    {{k_sweep_q<0, kBitpack, 128, 6>, k_sweep_q<1, kBitpack, 128, 6>}, 128, "queue-128x6"},
+    {{k_sweep_bp<0, 1, true, 256, 4>, k_sweep_bp<1, 1, true, 256, 4>}, 256, "ilp1-prefetch-256x4"},
+    {{k_sweep_bp<0, 2, true, 256, 2>, k_sweep_bp<1, 2, true, 256, 2>}, 256, "ilp2-prefetch-256x2"},
+    {{k_sweep_bp<0, 1, false, 256, 1>, k_sweep_bp<1, 1, false, 256, 1>}, 256, "ilp1-256"},
+    {{k_sweep_bp<0, 1, true, 128, 8>, k_sweep_bp<1, 1, true, 128, 8>}, 128, "ilp1-prefetch-128x8"},
+    {{k_sweep_bp<0, 2, true, 128, 4>, k_sweep_bp<1, 2, true, 128, 4>}, 128, "ilp2-prefetch-128x4"},
+};
+
+static const SweepVariant kI8Variants[] = {
+    {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, "queue-256x3"},
+    {{k_sweep_q<0, kInt8, 256, 4>, k_sweep_q<1, kInt8, 256, 4>}, 256, "queue-256x4"},
+    {{k_sweep_i8a<0, true, 256, 4>, k_sweep_i8a<1, true, 256, 4>}, 256, "prefetch-256x4"},
+    {{k_sweep_i8a<0, true, 256, 3>, k_sweep_i8a<1, true, 256, 3>}, 256, "prefetch-256x3"},
+    {{k_sweep_i8a<0, false, 256, 1>, k_sweep_i8a<1, false, 256, 1>}, 256, "plain-256"},
+    {{k_sweep_i8a<0, true, 128, 8>, k_sweep_i8a<1, true, 128, 8>}, 128, "prefetch-128x8"},
+};
+
+constexpr int kNumBpVariants = sizeof(kBpVariants) / sizeof(kBpVariants[0]);
+constexpr int kNumI8Variants = sizeof(kI8Variants) / sizeof(kI8Variants[0]);
+
+static std::atomic<int> g_bp_variant{0};
+static std::atomic<int> g_i8_variant{0};
+
+int sweep_variant_count(int layout) {
+    return layout == kBitpack ? kNumBpVariants : layout == kInt8 ? kNumI8Variants : 0;
+}
+
+const char* sweep_variant_name(int layout, int v) {
+    if (v < 0 || v >= sweep_variant_count(layout)) return nullptr;
+    return layout == kBitpack ? kBpVariants[v].name : kI8Variants[v].name;
+}
+
+int get_sweep_variant(int layout) {
+    return layout == kBitpack ? g_bp_variant.load() : g_i8_variant.load();
+}
+
+bool set_sweep_variant(int layout, int v) {
+    if (v < 0 || v >= sweep_variant_count(layout)) return false;
+    (layout == kBitpack ? g_bp_variant : g_i8_variant).store(v);
+    return true;
+}
+
 cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* dst,
                             const DrawParams& P, uint32_t hs, long long* obs_cur,
                             long long* obs_prev, long long* zero_slot, cudaStream_t st) {
     const SweepArgs a = sweep_args(g, src, dst, P, hs, obs_cur, half == 0 ? obs_prev : nullptr,
                                    zero_slot);
-    const int block = 256;
-    if (g.layout == kBitpack) {
-        if (half == 0) {
-            k_sweep_bp<0><<<grid_for(k_sweep_bp<0>, block, g.nblocks), block, 0, st>>>(a);
-        } else {
-            k_sweep_bp<1><<<grid_for(k_sweep_bp<1>, block, g.nblocks), block, 0, st>>>(a);
-        }
-    } else if (g.aligned) {
-        if (half == 0) {
-            k_sweep_i8<0, true><<<grid_for(k_sweep_i8<0, true>, block, g.nblocks), block, 0, st>>>(a);
-        } else {
-            k_sweep_i8<1, true><<<grid_for(k_sweep_i8<1, true>, block, g.nblocks), block, 0, st>>>(a);
-        }
+    if (g.layout == kBitpack || g.aligned) {
+        const SweepVariant& v = g.layout == kBitpack ? kBpVariants[g_bp_variant.load()]
+                                                     : kI8Variants[g_i8_variant.load()];
+        SweepKernel k = v.k[half];
+        k<<<grid_for(k, v.block, g.nblocks), v.block, 0, st>>>(a);
     } else {
+        const int block = 256;
         if (half == 0) {
-            k_sweep_i8<0, false><<<grid_for(k_sweep_i8<0, false>, block, g.nblocks), block, 0, st>>>(a);
+            k_sweep_i8g<0><<<grid_for(k_sweep_i8g<0>, block, g.nblocks), block, 0, st>>>(a);
         } else {
-            k_sweep_i8<1, false><<<grid_for(k_sweep_i8<1, false>, block, g.nblocks), block, 0, st>>>(a);
+            k_sweep_i8g<1><<<grid_for(k_sweep_i8g<1>, block, g.nblocks), block, 0, st>>>(a);
         }
     }
     return cudaGetLastError();

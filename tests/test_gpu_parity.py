@@ -75,9 +75,9 @@ def test_init_matches_oracle(orc, layout, L, kind):
 
 def test_strict_comparison_ties_on_the_gpu(orc):
     """A site uniform equal to its threshold is not below it (Algorithm 3's
-    strict rand() < p): with a complement-symmetric table set to a site's own
-    uniform that site must stay -1 (a + site) or come out +1... as the oracle
-    says; this drives the lazy comparison through all 32 random planes."""
+    strict rand() < p).  Complement-symmetric tables are set to a site's own
+    uniform (and one above it), for + and for - sites, and the GPU must agree
+    with the oracle; the tie drives the lazy comparison through all 32 planes."""
     L, seed, lat_id, hs = 64, 99, 3, 6
     for base_spin in (1, -1):
         src = np.full(L * L, base_spin, dtype=np.int8)
@@ -249,3 +249,27 @@ def test_run_argument_errors():
         lat.run(5)
     with pytest.raises(shk.ShakenError):
         lat.read_observables()
+
+
+@pytest.mark.parametrize("layout,L", [("bitpack", 96), ("bitpack", 1024), ("int8", 64), ("int8", 288)])
+def test_every_sweep_variant_draws_the_same_spins(orc, layout, L):
+    """The launch-shape variants the autotuner chooses from differ only in
+    speed: each one reproduces the oracle's half-step exactly."""
+    from paper_1908_07341_gb300 import tune
+    q, J, seed, lat_id = 0.7, 0.6, 99, 4
+    T = orc.thresholds(q, J)
+    src = random_spins(L, seed=L + 1)
+    before = tune.get_variant(layout)
+    try:
+        for v in range(len(tune.variant_names(layout))):
+            tune.set_variant(layout, v)
+            for half in (0, 1):
+                d_src = to_device_plane(src, L, layout)
+                d_dst = to_device_plane(np.ones(L * L, np.int8), L, layout)
+                acc = torch.zeros(5, dtype=torch.int64, device="cuda")
+                shk.halfstep(layout, half, d_src, d_dst, L, T, seed, lat_id, 2 * 5 + half, acc)
+                want = orc.halfstep(half, src, L, T, seed, lat_id, 2 * 5 + half)
+                assert np.array_equal(from_device_plane(d_dst, L, layout), want), (v, half)
+                assert np.array_equal(acc.cpu().numpy(), _orc_obs_halfstep(orc, half, src, want, L))
+    finally:
+        tune.set_variant(layout, before)
