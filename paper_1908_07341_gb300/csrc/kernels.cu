@@ -419,6 +419,157 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     finish_step<HALF>(acc, a);
 }
 
+// ------------------------------------------------------------ strip-walk sweep
+//
+// Planes with L % 1024 == 0 (rows of a multiple of 32 blocks).  A task is a
+// strip of 32 consecutive blocks (one per lane) over consecutive rows; every
+// warp of the grid gets an equal share of the rows of all strips (at most two
+// tasks).  The warp walks the rows
+// in the direction that makes the row neighbour the previous row it already
+// holds as bits (up for half-step A, which reads x^down; down for B, which
+// reads x^up).  The bit beside the block comes from the next lane by a shuffle,
+// and from one scalar load at the strip edge.  The next row is prefetched
+// while the current one is drawn.  Blocks undecided after two Philox calls go
+// through the same warp queue as in k_sweep_q.
+
+// One row of a lane's block as loaded: a word (bit-packed) or 32 bytes (int8).
+template <int LAYOUT>
+struct RowRaw;
+template <>
+struct RowRaw<kBitpack> {
+    uint32_t v;
+};
+template <>
+struct RowRaw<kInt8> {
+    uint4 lo, hi;
+};
+
+template <int LAYOUT>
+__device__ __forceinline__ RowRaw<LAYOUT> load_row(const void* src, uint32_t w) {
+    RowRaw<LAYOUT> r;
+    if constexpr (LAYOUT == kBitpack) {
+        r.v = __ldg(static_cast<const uint32_t*>(src) + w);
+    } else {
+        const uint4* p = reinterpret_cast<const uint4*>(static_cast<const int8_t*>(src) + 32 * (size_t)w);
+        r.lo = __ldg(p);
+        r.hi = __ldg(p + 1);
+    }
+    return r;
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ uint32_t row_bits(const RowRaw<LAYOUT>& r) {
+    if constexpr (LAYOUT == kBitpack) return r.v;
+    else return pack_up32(r.lo, r.hi);
+}
+
+// The field-neighbour bit just outside the strip in row `row`: bit 31 of the
+// block left of the strip (A) or bit 0 of the block right of it (B).
+template <int HALF, int LAYOUT>
+__device__ __forceinline__ uint32_t edge_bit(const void* src, uint32_t row, uint32_t edge_block, uint32_t W) {
+    const size_t b = (size_t)row * W + edge_block;
+    if constexpr (LAYOUT == kBitpack) {
+        const uint32_t v = __ldg(static_cast<const uint32_t*>(src) + b);
+        return HALF == 0 ? v >> 31 : v & 1u;
+    } else {
+        const int8_t* p = static_cast<const int8_t*>(src);
+        return (uint32_t)(__ldg(p + 32 * b + (HALF == 0 ? 31 : 0)) > 0);
+    }
+}
+
+template <int HALF, int LAYOUT, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) {
+    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    uint32_t head = 0;
+    int count = 0;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t W = a.Wr, L = a.L;
+    const uint32_t nstrips = W / 32;
+    const bool edge_lane = HALF == 0 ? lane == 0 : lane == 31;
+    // Warp g walks the row-strip indices [g T / G, (g+1) T / G) of the
+    // strip-major sequence (strip * L + row), T = nstrips * L, G = warps: equal
+    // shares, split where a strip ends.
+    const uint64_t total = (uint64_t)nstrips * L;
+    uint64_t pos = total * gwarp / nwarps;
+    const uint64_t end = total * (gwarp + 1) / nwarps;
+    while (pos < end) {
+        const uint32_t strip = (uint32_t)(pos / L);
+        const uint32_t r0 = (uint32_t)(pos - (uint64_t)strip * L);
+        const uint64_t left_here = end - pos, left_in_strip = L - r0;
+        const uint32_t nrows = (uint32_t)(left_here < left_in_strip ? left_here : left_in_strip);
+        pos += nrows;
+        const uint32_t col = strip * 32 + lane;
+        const uint32_t edge_block = HALF == 0 ? (strip == 0 ? W - 1 : strip * 32 - 1)
+                                              : (strip + 1 == nstrips ? 0 : strip * 32 + 32);
+        // rows in walk order: A ascends r0..r0+nrows-1, B descends
+        auto row_at = [&](uint32_t i) -> uint32_t { return HALF == 0 ? r0 + i : r0 + nrows - 1 - i; };
+        const uint32_t first = row_at(0);
+        const uint32_t nb_row = HALF == 0 ? (first == 0 ? L - 1 : first - 1) : (first + 1 == L ? 0 : first + 1);
+        uint32_t prev = row_bits<LAYOUT>(load_row<LAYOUT>(a.src, nb_row * W + col));
+        RowRaw<LAYOUT> cur = load_row<LAYOUT>(a.src, first * W + col);
+        uint32_t cur_edge = edge_lane ? edge_bit<HALF, LAYOUT>(a.src, first, edge_block, W) : 0u;
+        for (uint32_t i = 0; i < nrows; ++i) {
+            const uint32_t row = row_at(i);
+            RowRaw<LAYOUT> nxt{};
+            uint32_t nxt_edge = 0;
+            if (i + 1 < nrows) {                                      // prefetch the next row
+                const uint32_t r = row_at(i + 1);
+                nxt = load_row<LAYOUT>(a.src, r * W + col);
+                if (edge_lane) nxt_edge = edge_bit<HALF, LAYOUT>(a.src, r, edge_block, W);
+            }
+            const uint32_t S = row_bits<LAYOUT>(cur), N1 = prev;
+            uint32_t N2;
+            if (HALF == 0) {
+                const uint32_t left = __shfl_up_sync(0xffffffffu, S, 1) >> 31;
+                N2 = (S << 1) | (lane == 0 ? cur_edge : left);
+            } else {
+                const uint32_t right = __shfl_down_sync(0xffffffffu, S, 1) & 1u;
+                N2 = (S >> 1) | ((lane == 31 ? cur_edge : right) << 31);
+            }
+            const uint32_t w = row * W + col;
+            const BlockClass k = block_class(S, N1, N2);
+            uint32_t und, up;
+            draw_first_two(k, w, 0xffffffffu, a.hs, a.P, und, up);
+            const bool parked = und != 0u;
+            const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+            if (parked) {
+                const uint32_t qi = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+                q[0][qi] = w;
+                q[1][qi] = und;
+                q[2][qi] = up;
+                q[3][qi] = S;
+                q[4][qi] = N1;
+                q[5][qi] = N2;
+            } else {
+                finish_block<HALF, LAYOUT>(a, w, up, S, N1, N2, cnn, acc);
+            }
+            count += __popc(mask);
+            if (count >= 32) {
+                __syncwarp();
+                drain_queue<HALF, LAYOUT>(a, q, head, 32, cnn, acc);
+                __syncwarp();
+                head = (head + 32) & (kQueueCap - 1);
+                count -= 32;
+            }
+            prev = S;
+            cur = nxt;
+            cur_edge = nxt_edge;
+        }
+    }
+    if (count > 0) {
+        __syncwarp();
+        drain_queue<HALF, LAYOUT>(a, q, head, count, cnn, acc);
+    }
+    finish_step<HALF>(acc, a);
+}
+
 // int8 half-step for any L (site-by-site neighbour gathers; partial last block).
 template <int HALF>
 __global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {
@@ -725,6 +876,8 @@ struct SweepVariant {
 };
 
 static const SweepVariant kBpVariants[] = {
+    {{k_sweep_strip<0, kBitpack, 256, 3>, k_sweep_strip<1, kBitpack, 256, 3>}, 256, "strip-256x3"},
+    {{k_sweep_strip<0, kBitpack, 128, 6>, k_sweep_strip<1, kBitpack, 128, 6>}, 128, "strip-128x6"},
     {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, "queue-256x3"},
     {{k_sweep_q<0, kBitpack, 256, 4>, k_sweep_q<1, kBitpack, 256, 4>}, 256, "queue-256x4"},
     {{k_sweep_q<0, kBitpack, 128, 6>, k_sweep_q<1, kBitpack, 128, 6>}, 128, "queue-128x6"},
@@ -736,6 +889,8 @@ static const SweepVariant kBpVariants[] = {
 };
 
 static const SweepVariant kI8Variants[] = {
+    {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, "strip-256x3"},
+    {{k_sweep_strip<0, kInt8, 128, 6>, k_sweep_strip<1, kInt8, 128, 6>}, 128, "strip-128x6"},
     {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, "queue-256x3"},
     {{k_sweep_q<0, kInt8, 256, 4>, k_sweep_q<1, kInt8, 256, 4>}, 256, "queue-256x4"},
     {{k_sweep_i8a<0, true, 256, 4>, k_sweep_i8a<1, true, 256, 4>}, 256, "prefetch-256x4"},
@@ -745,6 +900,7 @@ static const SweepVariant kI8Variants[] = {
 };
 
 constexpr int kNumBpVariants = sizeof(kBpVariants) / sizeof(kBpVariants[0]);
+constexpr int kNumStripVariants = 2;   // the first entries of both tables
 constexpr int kNumI8Variants = sizeof(kI8Variants) / sizeof(kI8Variants[0]);
 
 static std::atomic<int> g_bp_variant{0};
@@ -772,13 +928,15 @@ bool set_sweep_variant(int layout, int v) {
 cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* dst,
                             const DrawParams& P, uint32_t hs, long long* obs_cur,
                             long long* obs_prev, long long* zero_slot, cudaStream_t st) {
-    const SweepArgs a = sweep_args(g, src, dst, P, hs, obs_cur, half == 0 ? obs_prev : nullptr,
-                                   zero_slot);
+    SweepArgs a = sweep_args(g, src, dst, P, hs, obs_cur, half == 0 ? obs_prev : nullptr, zero_slot);
     if (g.layout == kBitpack || g.aligned) {
-        const SweepVariant& v = g.layout == kBitpack ? kBpVariants[g_bp_variant.load()]
-                                                     : kI8Variants[g_i8_variant.load()];
+        int vi = g.layout == kBitpack ? g_bp_variant.load() : g_i8_variant.load();
+        // strip-walk variants need rows of a multiple of 32 blocks (L % 1024 == 0)
+        if (vi < kNumStripVariants && (g.Wr % 32) != 0) vi = kNumStripVariants;
+        const SweepVariant& v = g.layout == kBitpack ? kBpVariants[vi] : kI8Variants[vi];
         SweepKernel k = v.k[half];
-        k<<<grid_for(k, v.block, g.nblocks), v.block, 0, st>>>(a);
+        const int grid = grid_for(k, v.block, g.nblocks);
+        k<<<grid, v.block, 0, st>>>(a);
     } else {
         const int block = 256;
         if (half == 0) {
