@@ -361,6 +361,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "clocks": clocks,
         "wall_s_bitpack": wall,
     }
+    if not args.no_batched:
+        line["batched"] = bench_batched(dev, stream)
     if world == 1 and not args.no_cpu_baseline:
         rows = 8192
         rate, secs, units = _oracle_sample_rate(rows)
@@ -372,6 +374,63 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def bench_batched(dev, stream, plain_steps: int = 100):
+    """The phase-diagram batch (1024 lattices, uneven L, one (q, J) cell each,
+    10^4 steps, burn-in 5000) in the persistent graph-replayed kernel, and the
+    same lattices advanced by plain per-lattice shk_run calls on one stream for
+    plain_steps steps.  Returns a dict for the JSON line."""
+    import numpy as np
+    import torch
+
+    import paper_1908_07341_gb300 as shk
+    from paper_1908_07341_gb300 import tune, workloads
+    from paper_1908_07341_gb300.batch import Batch
+
+    w = workloads.phase_diagram_batch()
+    L = w["L"]
+    units_per_step = float((2 * L.astype(np.float64) ** 2).sum())
+    b = Batch(w["L"], w["q"], w["J"], w["seed"], w["lattice_id"], device=dev, stream=stream)
+    tuned = tune.autotune_batch(b, init_kind="random", init_seed=w["init_seed"])
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    b.run(w["steps"], burn_in=w["burn_in"])
+    e.record(stream)
+    torch.cuda.synchronize()
+    batched_ms = s.elapsed_time(e)
+    stats = b.read_stats()
+    assert int(stats[:, 10].min()) == w["steps"] - w["burn_in"]
+    b.close()
+    # plain per-lattice launches of the same lattices on one stream
+    lats = []
+    for i in range(len(L)):
+        lat = shk.Lattice(int(L[i]), "bitpack", device=dev, stream=stream)
+        lat.set_seed(int(w["seed"][i]), int(w["lattice_id"][i])).set_params(float(w["q"][i]), float(w["J"][i]))
+        lat.init("random", init_seed=w["init_seed"])
+        lats.append(lat)
+    for lat in lats:
+        lat.run(2)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for lat in lats:
+        lat.run(plain_steps)
+    e.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = s.elapsed_time(e)
+    for lat in lats:
+        lat.close()
+    batched_rate = units_per_step * w["steps"] / (batched_ms / 1e3)
+    plain_rate = units_per_step * plain_steps / (plain_ms / 1e3)
+    return {"workload": "1024 lattices, L log-uniform in {32..2048} (seeded), 32x32 (q,J) grid "
+                        "q in [0.05,3], J in [0.05,1.5], random starts, 10^4 steps, burn-in 5000",
+            "value": batched_rate, "unit": UNIT, "ms": batched_ms, "steps": w["steps"],
+            "site_updates": units_per_step * w["steps"],
+            "plain_value": plain_rate, "plain_steps_timed": plain_steps, "plain_ms": plain_ms,
+            "speedup_vs_plain": batched_rate / plain_rate, "tuned": list(tuned["best"]),
+            "launches": w["steps"] // tuned["best"][0]}
 
 
 def run_kernel_case(spec: str) -> int:
@@ -432,6 +491,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched phase-diagram line")
     ap.add_argument("--kernel-case", default=None,
                     help="LAYOUT:L:LAUNCHES -- only run half-step launches (for profiling)")
     args = ap.parse_args()

@@ -223,6 +223,51 @@ int shk_download_plane(shk_lattice* lat, int plane, void* host_raw, size_t bytes
 /* Device pointer of plane 0 (sigma) or 1 (tau) inside the handle's memory. */
 void* shk_plane_ptr(shk_lattice* lat, int plane);
 
+/* ------------------------------------------------------------ batched lattices */
+
+/* Many independent bit-packed lattices of uneven side L (32 <= L <= 65536,
+ * L % 32 == 0), each with its own (q, J), seed and lattice id (for example one
+ * lattice per cell of a (q, J) phase-diagram grid, as in Section 3.1 of the
+ * paper, which ran one (q, J) point per CPU thread).  One persistent kernel
+ * advances every lattice by steps_per_launch full steps per launch: each
+ * lattice is cut into tiles of whole rows (about tile_sites sites each); a CTA
+ * takes a tile and its halo rows into shared memory and steps it there.  The
+ * launch is captured once in a CUDA graph and replayed.  Every lattice follows
+ * exactly the trajectory shk_run would give it (same random numbers), and its
+ * five sums of every step t >= burn_in are folded into SHK_NSTATS exact int64
+ * statistics:
+ *   [0] sum M_sigma  [1] sum M_sigma^2  [2] sum |M_sigma|  [3] sum S_J
+ *   [4] sum S_q      [5] sum S_J^2      [6] sum S_q^2      [7] sum S_J*S_q
+ *   [8] sum C_nn     [9] sum C_nn^2    [10] number of steps added
+ * from which <m>, <|m|>, the susceptibility N(<m^2> - <m>^2) and the moments
+ * of H = -(J S_J + q S_q) follow exactly.  Device memory (shk_batch_bytes) is
+ * the caller's; the handle must not be used from two host threads at once. */
+#define SHK_NSTATS 11
+typedef struct shk_batch shk_batch;
+
+size_t shk_batch_bytes(int n, const int* L);
+int shk_batch_create(int n, const int* L, const double* q, const double* J, const uint64_t* seed,
+                     const uint32_t* lattice_id, void* dev_mem, size_t bytes, void* stream,
+                     shk_batch** out);
+void shk_batch_destroy(shk_batch* b);
+const char* shk_batch_last_error(const shk_batch* b);
+/* steps_per_launch in 1..32, block_threads in {128, 256, 512}, tile_sites >=
+ * 1024 (rows per tile = max(1, min(L, tile_sites / L))).  Defaults 8, 256,
+ * 2^18.  SHK_EINVAL if a tile would not fit in shared memory. */
+int shk_batch_configure(shk_batch* b, int steps_per_launch, int block_threads, int tile_sites);
+/* Initial state of every lattice (shk_init_plane with its lattice id); resets
+ * the step counter and the statistics. */
+int shk_batch_init(shk_batch* b, int kind, uint64_t init_seed);
+/* n_steps (a multiple of steps_per_launch) more steps of every lattice;
+ * asynchronous on the batch's stream. */
+int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in);
+int shk_batch_get_step(shk_batch* b, uint64_t* step);
+/* n x SHK_NSTATS statistics, n x SHK_NOBS sums of the last step, spins of one
+ * lattice (int8 +/-1, plane 0 = sigma, 1 = tau).  Synchronous. */
+int shk_batch_read_stats(shk_batch* b, int64_t* host_stats);
+int shk_batch_read_observables(shk_batch* b, int64_t* host_obs);
+int shk_batch_read_spins(shk_batch* b, int idx, int plane, int8_t* host_out);
+
 /* ------------------------------------------------------------ allocation-free run */
 
 /* Largest tau plane the library's own scratch array holds (8 MiB): bit-packed

@@ -19,6 +19,7 @@ BITPACK, INT8 = 1, 2
 INIT_ALL_UP, INIT_ALL_DOWN, INIT_RANDOM = 0, 1, 2
 HALF_A, HALF_B = 0, 1
 NOBS = 5
+NSTATS = 11
 MAX_L = 262144
 MAX_STEP = 0x80000000
 
@@ -54,6 +55,17 @@ SIGNATURES = {
     "shk_upload_plane": (_i, [_vp, _i, _vp, _sz]),
     "shk_download_plane": (_i, [_vp, _i, _vp, _sz]),
     "shk_plane_ptr": (_vp, [_vp, _i]),
+    "shk_batch_bytes": (_sz, [_i, _vp]),
+    "shk_batch_create": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "shk_batch_destroy": (None, [_vp]),
+    "shk_batch_last_error": (_c.c_char_p, [_vp]),
+    "shk_batch_configure": (_i, [_vp, _i, _i, _i]),
+    "shk_batch_init": (_i, [_vp, _i, _u64]),
+    "shk_batch_run": (_i, [_vp, _u64, _u64]),
+    "shk_batch_get_step": (_i, [_vp, _vp]),
+    "shk_batch_read_stats": (_i, [_vp, _vp]),
+    "shk_batch_read_observables": (_i, [_vp, _vp]),
+    "shk_batch_read_spins": (_i, [_vp, _i, _i, _vp]),
     "shk_shaken_run_static": (_i, [_i, _vp, _i, _d, _d, _u64, _u32, _u64, _u64, _vp, _vp]),
 }
 

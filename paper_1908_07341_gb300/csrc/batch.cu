@@ -1,0 +1,690 @@
+// batch.cu -- many independent lattices in one persistent launch.
+//
+// The paper's phase-diagram runs give every (q, J) point its own lattice and
+// thread (Section 4, multicore implementation).  Here a batch of bit-packed
+// lattices of uneven side L is advanced by one persistent kernel.  Every
+// lattice is cut into tiles of whole rows; a work item is one tile.  A launch
+// advances every tile by k full steps: the CTA loads the tile's sigma rows
+// together with k rows below and k + 1 rows above (wrapping around the torus)
+// into shared memory and runs k steps there.  Each full step narrows the
+// valid rows by one at each end (half-step A reads x^down, B reads x^up), so
+// after k steps sigma is exact on the tile plus one row above and tau on the
+// tile plus two rows above: enough for the observables of every step.  The
+// halo rows are recomputed rather than exchanged; the counter-based random
+// numbers make the recomputation exact.
+// A lattice small enough to be one tile keeps its whole torus in shared memory
+// with the rows wrapping, and needs no halo.
+//
+// sigma is double-buffered across launches (a tile reads the halo rows that
+// neighbouring tiles overwrite); tau is written but never read.  The five
+// observable sums of every step are added per tile into per-lattice partials;
+// the last tile of a lattice to finish (ticket counter) folds them into exact
+// int64 statistics; the last CTA of the launch advances the device-side step
+// counter and resets the work counter.  No CTA ever waits for another, so a
+// single kernel node can be replayed from a CUDA graph for the whole run.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "shaken.h"
+#include "internal.h"
+
+namespace shk {
+
+constexpr int kMaxStepsPerLaunch = 32;
+constexpr int kStatFields = SHK_NSTATS;
+static_assert(SHK_NSTATS == 11, "statistics layout");
+constexpr int kBatchQueueFields = 7;   // w, und, up, S, N1, N2, local index
+
+struct BatchLattice {
+    uint32_t L, Wr;             // side, words per row
+    uint32_t tile_rows;         // H
+    uint32_t ntiles;
+    unsigned long long sigma_off[2];   // byte offsets of the two sigma buffers
+    unsigned long long tau_off;
+    unsigned long long scratch_off;    // partials [kMaxStepsPerLaunch][5] int64, then the ticket
+    DrawParams P;
+};
+
+struct BatchItem {
+    uint32_t lattice, tile;
+};
+
+struct BatchState {
+    unsigned long long t;          // step index of the next launch
+    unsigned long long launches;   // launches completed (sigma buffer parity)
+    unsigned int next;             // work counter of the running launch
+    unsigned int done;             // CTAs finished in the running launch
+};
+
+struct BatchArgs {
+    unsigned char* arena;
+    const BatchLattice* lat;
+    const BatchItem* items;
+    uint32_t n_items;
+    uint32_t k;                    // full steps per launch
+    unsigned long long burn_in;    // steps t < burn_in are not added to the statistics
+    BatchState* state;
+    long long* stats;              // n_lattices x kStatFields
+    long long* last_obs;           // n_lattices x 5
+};
+
+// Draws rows [rlo, rhi) of dst (local row index) from src in shared memory.
+// HALF 0 reads the row below (rho - 1), HALF 1 the row above (rho + 1); the
+// left/right neighbour wraps within the row.  Random numbers use the global
+// block index (global row g = (r_base + rho) mod L).
+template <int HALF, int BLOCK>
+__device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, uint32_t rlo, uint32_t rhi,
+                                           uint32_t R, bool wrap, uint32_t Wr, uint32_t L, int64_t r_base,
+                                           uint32_t hs, const DrawParams& P, uint32_t (*q)[kQueueCap]) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lo = rlo * Wr, hi = rhi * Wr;
+    const uint32_t below = (1u << lane) - 1u;
+    uint32_t head = 0;
+    int count = 0;
+    auto global_block = [&](uint32_t i) -> uint32_t {
+        const uint32_t rho = i / Wr, c = i - rho * Wr;
+        int64_t g = (r_base + (int64_t)rho) % (int64_t)L;
+        if (g < 0) g += L;
+        return (uint32_t)g * Wr + c;
+    };
+    auto drain = [&](int n) {
+        const bool has = (int)lane < n;
+        const uint32_t e = (head + lane) & (kQueueCap - 1);
+        uint32_t w = 0, und = 0, up = 0, S = 0, N1 = 0, N2 = 0, i = 0;
+        if (has) {
+            w = q[0][e]; und = q[1][e]; up = q[2][e]; S = q[3][e]; N1 = q[4][e]; N2 = q[5][e]; i = q[6][e];
+        }
+        const uint32_t res = draw_rest(block_class(S, N1, N2), w, und, up, hs, P);
+        if (has) dst[i] = res;
+    };
+    for (uint32_t base = lo + warp * 32; base < hi; base += BLOCK) {
+        const uint32_t i = base + lane;
+        const bool in = i < hi;
+        uint32_t S = 0, N1 = 0, N2 = 0, w = 0;
+        if (in) {
+            const uint32_t rho = i / Wr, c = i - rho * Wr;
+            S = src[i];
+            if (HALF == 0) {
+                N1 = src[(rho == 0 && wrap ? R - 1 : rho - 1) * Wr + c];
+                const uint32_t prev = src[rho * Wr + (c == 0 ? Wr - 1 : c - 1)];
+                N2 = (S << 1) | (prev >> 31);
+            } else {
+                N1 = src[(rho + 1 == R && wrap ? 0 : rho + 1) * Wr + c];
+                const uint32_t next = src[rho * Wr + (c + 1 == Wr ? 0 : c + 1)];
+                N2 = (S >> 1) | (next << 31);
+            }
+            w = global_block(i);
+        }
+        const BlockClass k = block_class(S, N1, N2);
+        uint32_t und, up;
+        draw_first_two(k, w, in ? 0xffffffffu : 0u, hs, P, und, up);
+        const bool parked = und != 0u;
+        const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+        if (parked) {
+            const uint32_t e = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+            q[0][e] = w; q[1][e] = und; q[2][e] = up; q[3][e] = S; q[4][e] = N1; q[5][e] = N2; q[6][e] = i;
+        } else if (in) {
+            dst[i] = up;
+        }
+        count += __popc(mask);
+        if (count >= 32) {
+            __syncwarp();
+            drain(32);
+            __syncwarp();
+            head = (head + 32) & (kQueueCap - 1);
+            count -= 32;
+        }
+    }
+    if (count > 0) {
+        __syncwarp();
+        drain(count);
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchArgs a) {
+    extern __shared__ uint32_t tile_mem[];
+    __shared__ DrawParams P;
+    __shared__ uint32_t qbuf[BLOCK / 32][kBatchQueueFields][kQueueCap];
+    __shared__ long long red[kNumObs][BLOCK / 32];
+    __shared__ uint32_t item_sh;
+    __shared__ unsigned long long t0_sh, parity_sh;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t (*q)[kQueueCap] = qbuf[warp];
+    if (tid == 0) {
+        const volatile BatchState* vs = a.state;
+        t0_sh = vs->t;
+        parity_sh = vs->launches & 1ull;
+    }
+    __syncthreads();
+    const unsigned long long t0 = t0_sh;
+    const uint32_t par = (uint32_t)parity_sh;
+    const uint32_t k = a.k;
+
+    for (;;) {
+        if (tid == 0) item_sh = atomicAdd(&a.state->next, 1u);
+        __syncthreads();
+        const uint32_t ii = item_sh;
+        if (ii >= a.n_items) break;
+        const BatchItem it = a.items[ii];
+        const BatchLattice* B = a.lat + it.lattice;
+        const uint32_t L = B->L, Wr = B->Wr, H = B->tile_rows;
+        const uint32_t r0 = it.tile * H;
+        const uint32_t Hloc = min(H, L - r0);
+        // A lattice that is a single tile keeps its whole torus, rows wrapping;
+        // otherwise the tile carries rows r0-k .. r0+Hloc+k (k below, k+1 above).
+        const bool wrap = B->ntiles == 1;
+        const uint32_t R = wrap ? L : Hloc + 2 * k + 1;
+        const int64_t r_base = wrap ? 0 : (int64_t)r0 - (int64_t)k;
+        const uint32_t own_lo = wrap ? 0 : k;           // local rows of the tile itself
+        const uint32_t sweep_lo = wrap ? 0 : 1;
+        {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&B->P);
+            uint32_t* dstp = reinterpret_cast<uint32_t*>(&P);
+            for (uint32_t x = tid; x < sizeof(DrawParams) / 4; x += BLOCK) dstp[x] = src[x];
+        }
+        uint32_t* sg = tile_mem;
+        uint32_t* tu = tile_mem + R * Wr;
+        const uint32_t* sig_in = reinterpret_cast<const uint32_t*>(a.arena + B->sigma_off[par]);
+        for (uint32_t x = tid; x < R * Wr; x += BLOCK) {
+            const uint32_t rho = x / Wr, c = x - rho * Wr;
+            int64_t g = (r_base + (int64_t)rho) % (int64_t)L;
+            if (g < 0) g += L;
+            sg[x] = sig_in[(size_t)g * Wr + c];
+        }
+        __syncthreads();
+        long long* partial = reinterpret_cast<long long*>(a.arena + B->scratch_off);
+        for (uint32_t j = 0; j < k; ++j) {
+            const uint32_t hs = (uint32_t)(2 * (t0 + j));
+            tile_sweep<0, BLOCK>(sg, tu, sweep_lo, R, R, wrap, Wr, L, r_base, hs, P, q);
+            __syncthreads();
+            tile_sweep<1, BLOCK>(tu, sg, sweep_lo, wrap ? R : R - 1, R, wrap, Wr, L, r_base, hs + 1, P, q);
+            __syncthreads();
+            // sums over the tile's own rows
+            int v[kNumObs] = {0, 0, 0, 0, 0};
+            for (uint32_t x = own_lo * Wr + tid; x < (own_lo + Hloc) * Wr; x += BLOCK) {
+                const uint32_t rho = x / Wr, c = x - rho * Wr;
+                const uint32_t cr = rho * Wr + (c + 1 == Wr ? 0 : c + 1);
+                const uint32_t xu = (rho + 1 == R && wrap ? 0 : rho + 1) * Wr + c;
+                const uint32_t s = sg[x], t = tu[x];
+                const uint32_t sU = sg[xu], tU = tu[xu];
+                const uint32_t sR = (s >> 1) | (sg[cr] << 31), tR = (t >> 1) | (tu[cr] << 31);
+                v[0] += 2 * __popc(s) - 32;
+                v[1] += 2 * __popc(t) - 32;
+                v[2] += 32 - 2 * __popc(s ^ t);
+                v[3] += 64 - 2 * (__popc(s ^ tU) + __popc(s ^ tR));
+                v[4] += 64 - 2 * (__popc(s ^ sU) + __popc(s ^ sR));
+            }
+#pragma unroll
+            for (int f = 0; f < kNumObs; ++f) {
+                const int r = warp_sum(v[f]);
+                if (lane == 0) red[f][warp] = r;
+            }
+            __syncthreads();
+            if (warp == 0) {
+#pragma unroll
+                for (int f = 0; f < kNumObs; ++f) {
+                    long long r = lane < BLOCK / 32 ? red[f][lane] : 0;
+                    r = warp_sum64(r);
+                    if (lane == 0)
+                        atomicAdd(reinterpret_cast<unsigned long long*>(partial + j * kNumObs + f),
+                                  (unsigned long long)r);
+                }
+            }
+            __syncthreads();
+        }
+        // write the tile's rows of sigma (other buffer) and tau
+        uint32_t* sig_out = reinterpret_cast<uint32_t*>(a.arena + B->sigma_off[par ^ 1u]);
+        uint32_t* tau_out = reinterpret_cast<uint32_t*>(a.arena + B->tau_off);
+        for (uint32_t x = tid; x < Hloc * Wr; x += BLOCK) {
+            const uint32_t lx = x + own_lo * Wr;
+            const size_t gx = (size_t)r0 * Wr + x;
+            sig_out[gx] = sg[lx];
+            tau_out[gx] = tu[lx];
+        }
+        // the last tile of this lattice folds the k steps into the statistics
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            unsigned int* ticket = reinterpret_cast<unsigned int*>(partial + kMaxStepsPerLaunch * kNumObs);
+            const unsigned int tk = atomicAdd(ticket, 1u);
+            if (tk + 1 == B->ntiles) {
+                __threadfence();
+                long long* st = a.stats + (size_t)it.lattice * kStatFields;
+                for (uint32_t j = 0; j < k; ++j) {
+                    volatile long long* pj = partial + j * kNumObs;
+                    const long long M = pj[0], Mt = pj[1], Sq = pj[2], SJ = pj[3], C = pj[4];
+                    if (t0 + j >= a.burn_in) {
+                        st[0] += M;
+                        st[1] += M * M;
+                        st[2] += M < 0 ? -M : M;
+                        st[3] += SJ;
+                        st[4] += Sq;
+                        st[5] += SJ * SJ;
+                        st[6] += Sq * Sq;
+                        st[7] += SJ * Sq;
+                        st[8] += C;
+                        st[9] += C * C;
+                        st[10] += 1;
+                    }
+                    if (j + 1 == k) {
+                        long long* lo = a.last_obs + (size_t)it.lattice * kNumObs;
+                        lo[0] = M; lo[1] = Mt; lo[2] = Sq; lo[3] = SJ; lo[4] = C;
+                    }
+                    for (int f = 0; f < kNumObs; ++f) pj[f] = 0;
+                }
+                *ticket = 0u;
+                __threadfence();
+            }
+        }
+        __syncthreads();
+    }
+    // the last CTA of the launch prepares the next one
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int d = atomicAdd(&a.state->done, 1u);
+        if (d + 1 == gridDim.x) {
+            a.state->next = 0u;
+            a.state->done = 0u;
+            a.state->t += k;
+            a.state->launches += 1ull;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace shk
+
+using namespace shk;
+
+struct shk_batch {
+    int n = 0;
+    unsigned char* dev = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<int> L;
+    std::vector<BatchLattice> lat;
+    std::vector<double> q, J;
+    std::vector<uint64_t> seed;
+    std::vector<uint32_t> lattice_id;
+    // device-side pieces (offsets into dev)
+    size_t off_state = 0, off_lat = 0, off_items = 0, off_stats = 0, off_last = 0;
+    size_t items_capacity = 0;
+    uint32_t n_items = 0;
+    // configuration
+    uint64_t step = 0;        // host copy of the step counter
+    int k = 8;
+    int block = 256;
+    int tile_sites = 1 << 18;
+    bool dirty = true;        // descriptors / items must be re-uploaded
+    size_t smem_bytes = 0;
+    // graph of one launch
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_burn_in = ~0ull;
+    int graph_k = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_batch_err;
+
+int bfail(shk_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_batch_err = buf;
+    set_thread_error(buf);
+    return code;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr size_t kScratchPerLattice = 256 * ((kMaxStepsPerLaunch * kNumObs * 8 + 8 + 255) / 256);
+
+bool batch_layout(int n, const int* L, std::vector<size_t>* lat_offsets, size_t* total, size_t* off_state,
+                  size_t* off_lat, size_t* off_items, size_t* off_stats, size_t* off_last,
+                  size_t* items_capacity) {
+    size_t off = 0;
+    *off_state = off;
+    off += 256;
+    *off_lat = off;
+    off = align256(off + (size_t)n * sizeof(BatchLattice));
+    size_t cap = 0;
+    for (int i = 0; i < n; ++i) cap += (size_t)L[i];   // at most one tile per row
+    *items_capacity = cap;
+    *off_items = off;
+    off = align256(off + cap * sizeof(BatchItem));
+    *off_stats = off;
+    off = align256(off + (size_t)n * kStatFields * 8);
+    *off_last = off;
+    off = align256(off + (size_t)n * kNumObs * 8);
+    lat_offsets->resize(n);
+    for (int i = 0; i < n; ++i) {
+        Geometry g;
+        if (!make_geometry(L[i], kBitpack, &g)) return false;
+        (*lat_offsets)[i] = off;
+        off += 3 * g.plane_bytes + kScratchPerLattice;
+    }
+    *total = off;
+    return true;
+}
+
+// Builds the work items (largest tiles first) and the shared memory a tile needs.
+void build_items(shk_batch* b, std::vector<BatchItem>* items) {
+    items->clear();
+    size_t smem_words = 0;
+    for (int i = 0; i < b->n; ++i) {
+        BatchLattice& B = b->lat[i];
+        const uint32_t H = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(B.L, b->tile_sites / (int64_t)B.L));
+        B.tile_rows = H;
+        B.ntiles = (B.L + H - 1) / H;
+        for (uint32_t t = 0; t < B.ntiles; ++t) items->push_back({(uint32_t)i, t});
+        const uint32_t rows = B.ntiles == 1 ? B.L : H + 2 * b->k + 1;
+        smem_words = std::max<size_t>(smem_words, 2 * (size_t)rows * B.Wr);
+    }
+    std::stable_sort(items->begin(), items->end(), [&](const BatchItem& x, const BatchItem& y) {
+        const BatchLattice& A = b->lat[x.lattice];
+        const BatchLattice& C = b->lat[y.lattice];
+        const uint64_t wx = (uint64_t)std::min(A.tile_rows, A.L - x.tile * A.tile_rows) * A.L;
+        const uint64_t wy = (uint64_t)std::min(C.tile_rows, C.L - y.tile * C.tile_rows) * C.L;
+        return wx > wy;
+    });
+    b->smem_bytes = smem_words * 4;
+}
+
+// Shared-memory attribute and grid size (kept out of stream capture).
+template <int BLOCK>
+cudaError_t prepare_block(shk_batch* b, int* grid) {
+    cudaError_t e = cudaFuncSetAttribute(k_batch<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)b->smem_bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<BLOCK>, BLOCK, b->smem_bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *grid = (int)std::min<uint64_t>((uint64_t)per_sm * sm_count(), std::max<uint32_t>(1, b->n_items));
+    return cudaSuccess;
+}
+
+cudaError_t prepare_batch(shk_batch* b, int* grid) {
+    switch (b->block) {
+        case 128: return prepare_block<128>(b, grid);
+        case 512: return prepare_block<512>(b, grid);
+        default: return prepare_block<256>(b, grid);
+    }
+}
+
+cudaError_t launch_batch(shk_batch* b, int grid, uint64_t burn_in, cudaStream_t st) {
+    BatchArgs args;
+    args.arena = b->dev;
+    args.lat = reinterpret_cast<const BatchLattice*>(b->dev + b->off_lat);
+    args.items = reinterpret_cast<const BatchItem*>(b->dev + b->off_items);
+    args.n_items = b->n_items;
+    args.k = (uint32_t)b->k;
+    args.burn_in = burn_in;
+    args.state = reinterpret_cast<BatchState*>(b->dev + b->off_state);
+    args.stats = reinterpret_cast<long long*>(b->dev + b->off_stats);
+    args.last_obs = reinterpret_cast<long long*>(b->dev + b->off_last);
+    switch (b->block) {
+        case 128: k_batch<128><<<grid, 128, b->smem_bytes, st>>>(args); break;
+        case 512: k_batch<512><<<grid, 512, b->smem_bytes, st>>>(args); break;
+        default: k_batch<256><<<grid, 256, b->smem_bytes, st>>>(args); break;
+    }
+    return cudaGetLastError();
+}
+
+int upload_descriptors(shk_batch* b) {
+    std::vector<BatchItem> items;
+    build_items(b, &items);
+    if (items.size() > b->items_capacity) return bfail(b, SHK_EINVAL, "shk_batch: too many tiles");
+    b->n_items = (uint32_t)items.size();
+    cudaError_t e = cudaMemcpyAsync(b->dev + b->off_lat, b->lat.data(), b->lat.size() * sizeof(BatchLattice),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->dev + b->off_items, items.data(), items.size() * sizeof(BatchItem),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch upload: %s", cudaGetErrorString(e));
+    b->dirty = false;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return SHK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t shk_batch_bytes(int n, const int* L) {
+    if (n <= 0 || L == nullptr) return 0;
+    std::vector<size_t> lo;
+    size_t total, a, b2, c, d, e, cap;
+    if (!batch_layout(n, L, &lo, &total, &a, &b2, &c, &d, &e, &cap)) return 0;
+    return total;
+}
+
+int shk_batch_create(int n, const int* L, const double* q, const double* J, const uint64_t* seed,
+                     const uint32_t* lattice_id, void* dev_mem, size_t bytes, void* stream,
+                     shk_batch** out) {
+    if (out == nullptr) return bfail(nullptr, SHK_EINVAL, "shk_batch_create: out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !L || !q || !J || !seed || !lattice_id)
+        return bfail(nullptr, SHK_EINVAL, "shk_batch_create: n must be positive and arrays non-NULL");
+    for (int i = 0; i < n; ++i)
+        if (L[i] < 32 || L[i] % 32 != 0 || L[i] > 65536)
+            return bfail(nullptr, SHK_EINVAL, "shk_batch_create: lattice %d has L=%d (need 32 <= L <= 65536, L %% 32 == 0)",
+                         i, L[i]);
+    std::vector<size_t> lat_off;
+    size_t total, off_state, off_lat, off_items, off_stats, off_last, cap;
+    batch_layout(n, L, &lat_off, &total, &off_state, &off_lat, &off_items, &off_stats, &off_last, &cap);
+    if (dev_mem == nullptr || (reinterpret_cast<uintptr_t>(dev_mem) & 255u) != 0)
+        return bfail(nullptr, SHK_EINVAL, "shk_batch_create: dev_mem must be non-NULL and 256-byte aligned");
+    if (bytes < total) return bfail(nullptr, SHK_ENOMEM, "shk_batch_create: %zu bytes given, %zu needed", bytes, total);
+    shk_batch* b = new (std::nothrow) shk_batch();
+    if (!b) return bfail(nullptr, SHK_ENOMEM, "shk_batch_create: host allocation failed");
+    b->n = n;
+    b->dev = static_cast<unsigned char*>(dev_mem);
+    b->bytes = bytes;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->L.assign(L, L + n);
+    b->q.assign(q, q + n);
+    b->J.assign(J, J + n);
+    b->seed.assign(seed, seed + n);
+    b->lattice_id.assign(lattice_id, lattice_id + n);
+    b->off_state = off_state;
+    b->off_lat = off_lat;
+    b->off_items = off_items;
+    b->off_stats = off_stats;
+    b->off_last = off_last;
+    b->items_capacity = cap;
+    b->lat.resize(n);
+    for (int i = 0; i < n; ++i) {
+        Geometry g;
+        make_geometry(L[i], kBitpack, &g);
+        BatchLattice& B = b->lat[i];
+        std::memset(&B, 0, sizeof B);
+        B.L = (uint32_t)L[i];
+        B.Wr = g.Wr;
+        B.sigma_off[0] = lat_off[i];
+        B.sigma_off[1] = lat_off[i] + g.plane_bytes;
+        B.tau_off = lat_off[i] + 2 * g.plane_bytes;
+        B.scratch_off = lat_off[i] + 3 * g.plane_bytes;
+        uint32_t T[6];
+        if (host_thresholds(q[i], J[i], T) != SHK_OK) {
+            delete b;
+            return bfail(nullptr, SHK_EINVAL, "shk_batch_create: lattice %d has non-finite q or J", i);
+        }
+        make_draw_params(seed[i], lattice_id[i], T, 0u, &B.P);
+    }
+    // zero the state, statistics, results and per-lattice scratch
+    cudaError_t e = cudaMemsetAsync(b->dev, 0, total, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return bfail(nullptr, SHK_ECUDA, "shk_batch_create: %s", cudaGetErrorString(e));
+    }
+    const int rc = upload_descriptors(b);
+    if (rc != SHK_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SHK_OK;
+}
+
+void shk_batch_destroy(shk_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete b;
+}
+
+const char* shk_batch_last_error(const shk_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+int shk_batch_configure(shk_batch* b, int steps_per_launch, int block_threads, int tile_sites) {
+    if (!b) return bfail(nullptr, SHK_EINVAL, "shk_batch_configure: NULL handle");
+    if (steps_per_launch < 1 || steps_per_launch > kMaxStepsPerLaunch)
+        return bfail(b, SHK_EINVAL, "shk_batch_configure: steps_per_launch must be in 1..%d", kMaxStepsPerLaunch);
+    if (block_threads != 128 && block_threads != 256 && block_threads != 512)
+        return bfail(b, SHK_EINVAL, "shk_batch_configure: block_threads must be 128, 256 or 512");
+    if (tile_sites < 1024) return bfail(b, SHK_EINVAL, "shk_batch_configure: tile_sites must be >= 1024");
+    b->k = steps_per_launch;
+    b->block = block_threads;
+    b->tile_sites = tile_sites;
+    const int rc = upload_descriptors(b);
+    if (rc != SHK_OK) return rc;
+    // refuse a tile that does not fit in shared memory
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t static_smem = sizeof(DrawParams) + (size_t)(block_threads / 32) * (kBatchQueueFields * kQueueCap * 4 + kNumObs * 8) + 64;
+    if (b->smem_bytes + static_smem > (size_t)optin)
+        return bfail(b, SHK_EINVAL, "shk_batch_configure: a tile needs %zu bytes of shared memory (limit %d); lower tile_sites or steps_per_launch",
+                     b->smem_bytes + static_smem, optin);
+    return SHK_OK;
+}
+
+int shk_batch_init(shk_batch* b, int kind, uint64_t init_seed) {
+    if (!b) return bfail(nullptr, SHK_EINVAL, "shk_batch_init: NULL handle");
+    for (int i = 0; i < b->n; ++i) {
+        const int rc = shk_init_plane(SHK_BITPACK, b->dev + b->lat[i].sigma_off[0], b->L[i], kind, init_seed,
+                                      b->lattice_id[i], 0, b->stream);
+        if (rc != SHK_OK) return bfail(b, rc, "shk_batch_init: %s", shk_last_error(nullptr));
+        const int rc2 = shk_init_plane(SHK_BITPACK, b->dev + b->lat[i].tau_off, b->L[i], kind, init_seed,
+                                       b->lattice_id[i], 1, b->stream);
+        if (rc2 != SHK_OK) return bfail(b, rc2, "shk_batch_init: %s", shk_last_error(nullptr));
+    }
+    // state, statistics and last observables back to zero; sigma in buffer 0
+    cudaError_t e = cudaMemsetAsync(b->dev + b->off_state, 0, 256, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->dev + b->off_stats, 0, (size_t)b->n * kStatFields * 8, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->dev + b->off_last, 0, (size_t)b->n * kNumObs * 8, b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_init: %s", cudaGetErrorString(e));
+    b->step = 0;
+    return SHK_OK;
+}
+
+int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
+    if (!b) return bfail(nullptr, SHK_EINVAL, "shk_batch_run: NULL handle");
+    if (n_steps == 0) return SHK_OK;
+    if (b->step + n_steps > SHK_MAX_STEP)
+        return bfail(b, SHK_EINVAL, "shk_batch_run: step counter would exceed 2^31");
+    if (n_steps % (uint64_t)b->k != 0)
+        return bfail(b, SHK_EINVAL, "shk_batch_run: n_steps=%llu is not a multiple of steps_per_launch=%d",
+                     (unsigned long long)n_steps, b->k);
+    if (b->dirty) {
+        const int rc = upload_descriptors(b);
+        if (rc != SHK_OK) return rc;
+    }
+    cudaError_t e;
+    if (b->graph == nullptr || b->graph_burn_in != burn_in || b->graph_k != b->k) {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        int grid = 0;
+        e = prepare_batch(b, &grid);
+        if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run: %s", cudaGetErrorString(e));
+        cudaStream_t cap;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run: %s", cudaGetErrorString(e));
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t le = launch_batch(b, grid, burn_in, cap);
+            e = cudaStreamEndCapture(cap, &g);
+            if (le != cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run graph: %s", cudaGetErrorString(e));
+        b->graph_burn_in = burn_in;
+        b->graph_k = b->k;
+    }
+    for (uint64_t s = 0; s < n_steps; s += (uint64_t)b->k) {
+        e = cudaGraphLaunch(b->graph, b->stream);
+        if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run launch: %s", cudaGetErrorString(e));
+        b->step += (uint64_t)b->k;
+    }
+    return SHK_OK;
+}
+
+int shk_batch_read_stats(shk_batch* b, int64_t* host_stats) {
+    if (!b || !host_stats) return bfail(b, SHK_EINVAL, "shk_batch_read_stats: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(host_stats, b->dev + b->off_stats, (size_t)b->n * kStatFields * 8,
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_read_stats: %s", cudaGetErrorString(e));
+    return SHK_OK;
+}
+
+int shk_batch_read_observables(shk_batch* b, int64_t* host_obs) {
+    if (!b || !host_obs) return bfail(b, SHK_EINVAL, "shk_batch_read_observables: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(host_obs, b->dev + b->off_last, (size_t)b->n * kNumObs * 8,
+                                    cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_read_observables: %s", cudaGetErrorString(e));
+    return SHK_OK;
+}
+
+int shk_batch_get_step(shk_batch* b, uint64_t* step) {
+    if (!b || !step) return bfail(b, SHK_EINVAL, "shk_batch_get_step: NULL argument");
+    BatchState s;
+    cudaError_t e = cudaMemcpyAsync(&s, b->dev + b->off_state, sizeof s, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_get_step: %s", cudaGetErrorString(e));
+    *step = s.t;
+    return SHK_OK;
+}
+
+int shk_batch_read_spins(shk_batch* b, int idx, int plane, int8_t* host_out) {
+    if (!b || !host_out || idx < 0 || idx >= b->n || (plane != 0 && plane != 1))
+        return bfail(b, SHK_EINVAL, "shk_batch_read_spins: bad argument");
+    BatchState s;
+    cudaError_t e = cudaMemcpyAsync(&s, b->dev + b->off_state, sizeof s, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_read_spins: %s", cudaGetErrorString(e));
+    const BatchLattice& B = b->lat[idx];
+    const size_t off = plane == 0 ? B.sigma_off[s.launches & 1ull] : B.tau_off;
+    const int64_t N = (int64_t)B.L * B.L;
+    std::vector<uint32_t> words((size_t)(N / 32));
+    e = cudaMemcpyAsync(words.data(), b->dev + off, words.size() * 4, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_read_spins: %s", cudaGetErrorString(e));
+    for (int64_t u = 0; u < N; ++u) host_out[u] = ((words[u >> 5] >> (u & 31)) & 1u) ? 1 : -1;
+    return SHK_OK;
+}
+
+}  // extern "C"

@@ -143,6 +143,10 @@ __device__ __forceinline__ void draw_blocks(const uint32_t (&S)[K], const uint32
 // from call 2 with the lazy early exit.  The result is the same comparison,
 // bit for bit.
 
+// Capacity of a warp's ring of parked blocks: a power of two; at most 31 + 32
+// entries are held (a drain starts as soon as 32 are waiting).
+constexpr int kQueueCap = 64;
+
 // Class masks of a block (see draw_blocks).
 struct BlockClass {
     uint32_t F, Cg, C2;

@@ -324,7 +324,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_i8a(const SweepArgs a) {
 // words).  Blocks still undecided after Philox calls 0 and 1 wait there; once
 // 32 are waiting the warp continues them together from call 2 (draw_rest).
 
-constexpr int kQueueCap = 64;   // power of two; at most 31 + 32 entries are held
 constexpr int kQueueFields = 6;
 
 template <int HALF, int LAYOUT>

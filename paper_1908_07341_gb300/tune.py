@@ -120,3 +120,34 @@ def autotune(layout, L: int, use_cache: bool = True, stream=None) -> int:
             _store_cache(cache)
         set_variant(layout, best)
     return best
+
+
+def autotune_batch(batch, steps_per_launch=(2, 4, 8, 16), block_threads=(256, 512),
+                   tile_sites=(1 << 16, 1 << 17, 1 << 18, 1 << 19), launches: int = 3,
+                   init_kind="random", init_seed: int = 0) -> dict:
+    """Times every (steps per launch, block size, tile size) on a few launches
+    of the given batch and configures the fastest.  The batch is left
+    re-initialised (kind, init_seed) with its step counter at 0.  Returns
+    {"best": (k, block, tile_sites), "ms_per_step": {...}}."""
+    results = {}
+    stream = batch.stream
+    for k in steps_per_launch:
+        for blk in block_threads:
+            for ts in tile_sites:
+                try:
+                    batch.configure(k, blk, ts)
+                except _lib.ShakenError:
+                    continue            # tile does not fit in shared memory
+                batch.init(init_kind, init_seed)
+                batch.run(k)            # warm-up launch (graph capture)
+                s = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                batch.run(k * launches)
+                e.record(stream)
+                torch.cuda.synchronize()
+                results[(k, blk, ts)] = s.elapsed_time(e) / (k * launches)
+    best = min(results, key=results.get)
+    batch.configure(*best)
+    batch.init(init_kind, init_seed)
+    return {"best": best, "ms_per_step": {f"{k}/{b}/{t}": v for (k, b, t), v in results.items()}}

@@ -1,0 +1,23 @@
+"""Seeded synthetic workloads (inputs only: no arithmetic of the method).
+
+phase_diagram_batch reproduces the batched configuration: 1024 lattices, side
+L_k drawn log-uniformly from {32, 64, ..., 2048} by a seeded generator, cell
+k of a 32 x 32 (q, J) grid with q in [0.05, 3.0] and J in [0.05, 1.5], seed 4,
+lattice id k, random starts, 10^4 steps with the first half as burn-in.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def phase_diagram_batch(n_side: int = 32, seed: int = 4, q_range=(0.05, 3.0), J_range=(0.05, 1.5),
+                        L_choices=(32, 64, 128, 256, 512, 1024, 2048)) -> dict:
+    n = n_side * n_side
+    k = np.arange(n)
+    i, j = k // n_side, k % n_side
+    q = q_range[0] + i * (q_range[1] - q_range[0]) / (n_side - 1)
+    J = J_range[0] + j * (J_range[1] - J_range[0]) / (n_side - 1)
+    rng = np.random.default_rng(seed)
+    L = np.asarray(L_choices, dtype=np.int32)[rng.integers(0, len(L_choices), size=n)]
+    return {"L": L, "q": q, "J": J, "seed": np.full(n, seed, dtype=np.uint64),
+            "lattice_id": k.astype(np.uint32), "init_seed": seed, "steps": 10_000, "burn_in": 5_000}

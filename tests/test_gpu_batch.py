@@ -1,0 +1,101 @@
+"""Batched lattices (one persistent kernel, graph-replayed) against single-
+lattice runs: every lattice of a batch must follow exactly the trajectory
+shk_run gives it, and the batch statistics must equal the sums of the single
+runs' per-step observables (all integers, compared exactly).  The single-
+lattice path is itself checked against the oracle in test_gpu_parity."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1908_07341_gb300 as shk
+from paper_1908_07341_gb300.batch import Batch, derived, stats_from_observables
+from paper_1908_07341_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1908_07341_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _single(L, q, J, seed, lat_id, init_seed, n):
+    lat = shk.Lattice(int(L), "bitpack").set_seed(int(seed), int(lat_id)).set_params(float(q), float(J))
+    lat.init("random", init_seed=init_seed)
+    obs = lat.run(n, obs=True).cpu().numpy()
+    return obs, lat.read_spins(0), lat.read_spins(1)
+
+
+MIXED = dict(L=[32, 64, 96, 128, 160, 256, 32, 64],
+             q=[1.0, 0.5, 0.6585, 3.0, 0.05, 0.8, 2.0, 0.3],
+             J=[0.25, 0.5, 0.6585, 0.44, 1.7, 0.6, 0.1, 1.2],
+             seed=[1, 2, 3, 4, 5, 6, 7, 2 ** 40 + 9],
+             lattice_id=[0, 1, 2, 3, 4, 5, 6, 7])
+
+
+@pytest.mark.parametrize("k,block,tile_sites", [(1, 256, 1 << 18), (3, 128, 1024), (8, 256, 4096),
+                                                (8, 512, 1 << 18), (4, 256, 2048)])
+def test_batch_equals_single_lattice_runs(k, block, tile_sites):
+    n, burn = 24, 10
+    b = Batch(**MIXED).configure(k, block, tile_sites).init("random", init_seed=11)
+    b.run(n, burn_in=burn)
+    assert b.step == n
+    stats, last = b.read_stats(), b.read_observables()
+    for i in range(b.n):
+        obs, s, t = _single(MIXED["L"][i], MIXED["q"][i], MIXED["J"][i], MIXED["seed"][i],
+                            MIXED["lattice_id"][i], 11, n)
+        assert np.array_equal(b.read_spins(i, 0), s), i
+        assert np.array_equal(b.read_spins(i, 1), t), i
+        assert np.array_equal(last[i], obs[-1]), i
+        assert np.array_equal(stats[i], stats_from_observables(obs[burn:])), i
+
+
+def test_batch_large_tiles_and_resume():
+    """L = 1024 and 2048 cut into several tiles; 16 + 16 steps equal 32."""
+    cfg = dict(L=[2048, 1024, 512], q=[1.0, 0.7, 0.5], J=[0.35, 0.6, 0.9], seed=[3, 3, 3],
+               lattice_id=[10, 11, 12])
+    b = Batch(**cfg).configure(8, 256, 1 << 17).init("random", init_seed=3)
+    b.run(16, burn_in=0)
+    b.run(16, burn_in=0)
+    stats, last = b.read_stats(), b.read_observables()
+    for i in range(3):
+        obs, s, t = _single(cfg["L"][i], cfg["q"][i], cfg["J"][i], 3, cfg["lattice_id"][i], 3, 32)
+        assert np.array_equal(b.read_spins(i, 0), s), i
+        assert np.array_equal(b.read_spins(i, 1), t), i
+        assert np.array_equal(last[i], obs[-1])
+        assert np.array_equal(stats[i], stats_from_observables(obs))
+
+
+def test_phase_diagram_subset_matches_single_runs():
+    """A 64-lattice slice of the phase-diagram workload (uneven L, its own
+    (q, J) cell each) with burn-in, checked lattice by lattice."""
+    w = workloads.phase_diagram_batch()
+    idx = np.arange(0, 1024, 16)
+    cfg = {key: w[key][idx] for key in ("L", "q", "J", "seed", "lattice_id")}
+    n, burn = 40, 20
+    b = Batch(**cfg).configure(8, 256, 1 << 18).init("random", init_seed=w["init_seed"])
+    b.run(n, burn_in=burn)
+    stats = b.read_stats()
+    for i in range(0, len(idx), 4):
+        obs, s, _ = _single(cfg["L"][i], cfg["q"][i], cfg["J"][i], cfg["seed"][i], cfg["lattice_id"][i],
+                            w["init_seed"], n)
+        assert np.array_equal(stats[i], stats_from_observables(obs[burn:])), i
+        assert np.array_equal(b.read_spins(i, 0), s), i
+    d = derived(stats, cfg["L"], cfg["q"], cfg["J"])
+    assert np.all(np.abs(d["m"]) <= 1) and np.all(d["chi"] >= 0)
+
+
+def test_batch_argument_errors():
+    b = Batch(L=[64, 32], q=[1.0, 1.0], J=[0.3, 0.3], seed=[1, 1], lattice_id=[0, 1])
+    with pytest.raises(shk.ShakenError):
+        b.configure(0, 256, 1 << 18)
+    with pytest.raises(shk.ShakenError):
+        b.configure(8, 100, 1 << 18)
+    b.configure(8, 256, 1 << 18).init("up")
+    with pytest.raises(shk.ShakenError):
+        b.run(12)          # not a multiple of steps_per_launch
+    with pytest.raises(ValueError):
+        Batch(L=[33], q=[1.0], J=[0.3], seed=[1], lattice_id=[0])

@@ -107,3 +107,21 @@ def test_handle_state_checks_without_a_gpu(so):
         assert so.shk_plane_ptr(h, 1) == (1 << 20) + 512
     finally:
         so.shk_lattice_destroy(h)
+
+
+def test_batch_arguments_are_checked_without_a_gpu(so):
+    L = np.array([64, 2048, 32], dtype=np.int32)
+    need = so.shk_batch_bytes(3, L.ctypes.data)
+    assert need > 3 * (2048 * 2048 // 8)
+    bad = np.array([64, 33], dtype=np.int32)
+    assert so.shk_batch_bytes(2, bad.ctypes.data) == 0
+    q = np.ones(3)
+    J = np.ones(3)
+    seed = np.zeros(3, dtype=np.uint64)
+    ids = np.zeros(3, dtype=np.uint32)
+    h = ctypes.c_void_p()
+    assert so.shk_batch_create(3, L.ctypes.data, q.ctypes.data, J.ctypes.data, seed.ctypes.data,
+                               ids.ctypes.data, 256, 1024, None, ctypes.byref(h)) == _lib.ENOMEM
+    assert so.shk_batch_create(2, bad.ctypes.data, q.ctypes.data, J.ctypes.data, seed.ctypes.data,
+                               ids.ctypes.data, 256, 1 << 30, None, ctypes.byref(h)) == _lib.EINVAL
+    assert b"L=33" in so.shk_last_error(None)
