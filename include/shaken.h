@@ -268,6 +268,59 @@ int shk_batch_read_stats(shk_batch* b, int64_t* host_stats);
 int shk_batch_read_observables(shk_batch* b, int64_t* host_obs);
 int shk_batch_read_spins(shk_batch* b, int idx, int plane, int8_t* host_out);
 
+/* ------------------------------------------------------------ serving */
+
+/* A simulation request: one bit-packed lattice pair of side L (32 <= L <=
+ * 8192, L % 32 == 0) run for n_steps full steps from an initial state, with
+ * the statistics of the steps t >= burn_in (as in shk_batch). */
+typedef struct {
+    int L;
+    double q, J;
+    uint64_t seed;
+    uint32_t lattice_id;
+    int init_kind;          /* SHK_INIT_* */
+    uint64_t init_seed;
+    uint64_t n_steps;
+    uint64_t burn_in;
+} shk_job;
+
+/* A finished (or cancelled) job.  sigma_hash is the 64-bit FNV-1a hash of the
+ * final sigma plane's bytes (bit-packed layout); ticks count scheduler ticks. */
+typedef struct {
+    uint64_t job_id;
+    int status;             /* SHK_OK or SHK_ECANCELLED */
+    uint64_t steps_done;
+    int64_t stats[SHK_NSTATS];
+    int64_t last_obs[SHK_NOBS];
+    uint64_t sigma_hash;
+    uint64_t submit_tick, admit_tick, done_tick;
+} shk_result;
+
+/* Continuous batching of jobs (no counterpart in the paper, which ran a fixed
+ * grid of (q, J) points).  Queued jobs are admitted oldest first at each tick
+ * while a slot is free and the job's device memory (three planes and a small
+ * scratch) fits both the caller's arena and hbm_budget; every active job is
+ * then advanced by min(steps_per_tick, remaining) steps in one launch of the
+ * batched kernel, its lattice, step counter and random-number key resident on
+ * the device; finished jobs are retired with exact statistics.  A job's result
+ * is independent of the other jobs in the mix.  shk_server_tick is
+ * synchronous (it waits for the tick's launch); shk_server_submit never
+ * blocks (SHK_EBUSY when max_pending jobs already wait). */
+typedef struct shk_server shk_server;
+size_t shk_server_bytes(int max_slots, size_t arena_bytes);
+int shk_server_create(int max_slots, size_t hbm_budget, void* dev_mem, size_t bytes, void* stream,
+                      shk_server** out);
+void shk_server_destroy(shk_server* s);
+const char* shk_server_last_error(const shk_server* s);
+/* Defaults: 16 steps per tick, 256 threads, 2^17 sites per tile, 2^20 queued. */
+int shk_server_configure(shk_server* s, int steps_per_tick, int block_threads, int tile_sites,
+                         size_t max_pending);
+int shk_server_submit(shk_server* s, const shk_job* job, uint64_t* job_id);
+int shk_server_cancel(shk_server* s, uint64_t job_id);
+int shk_server_tick(shk_server* s, int* n_active, int* n_pending);
+int shk_server_poll(shk_server* s, shk_result* out, int max, int* n_out);
+int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes);
+
 /* ------------------------------------------------------------ allocation-free run */
 
 /* Largest tau plane the library's own scratch array holds (8 MiB): bit-packed

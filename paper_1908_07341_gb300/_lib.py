@@ -66,6 +66,16 @@ SIGNATURES = {
     "shk_batch_read_stats": (_i, [_vp, _vp]),
     "shk_batch_read_observables": (_i, [_vp, _vp]),
     "shk_batch_read_spins": (_i, [_vp, _i, _i, _vp]),
+    "shk_server_bytes": (_sz, [_i, _sz]),
+    "shk_server_create": (_i, [_i, _sz, _vp, _sz, _vp, _vp]),
+    "shk_server_destroy": (None, [_vp]),
+    "shk_server_last_error": (_c.c_char_p, [_vp]),
+    "shk_server_configure": (_i, [_vp, _i, _i, _i, _sz]),
+    "shk_server_submit": (_i, [_vp, _vp, _vp]),
+    "shk_server_cancel": (_i, [_vp, _u64]),
+    "shk_server_tick": (_i, [_vp, _vp, _vp]),
+    "shk_server_poll": (_i, [_vp, _vp, _i, _vp]),
+    "shk_server_stats": (_i, [_vp, _vp, _vp]),
     "shk_shaken_run_static": (_i, [_i, _vp, _i, _d, _d, _u64, _u32, _u64, _u64, _vp, _vp]),
 }
 

@@ -48,6 +48,10 @@ struct BatchLattice {
     unsigned long long sigma_off[2];   // byte offsets of the two sigma buffers
     unsigned long long tau_off;
     unsigned long long scratch_off;    // partials [kMaxStepsPerLaunch][5] int64, then the ticket
+    unsigned long long t;              // next step of this lattice (advanced on the device)
+    unsigned long long burn_in;        // steps t < burn_in are not added to the statistics
+    uint32_t parity;                   // sigma buffer holding the current state (flipped on the device)
+    uint32_t k_this;                   // full steps this launch (1..kMaxStepsPerLaunch)
     DrawParams P;
 };
 
@@ -56,19 +60,16 @@ struct BatchItem {
 };
 
 struct BatchState {
-    unsigned long long t;          // step index of the next launch
-    unsigned long long launches;   // launches completed (sigma buffer parity)
+    unsigned long long launches;   // launches completed
     unsigned int next;             // work counter of the running launch
     unsigned int done;             // CTAs finished in the running launch
 };
 
 struct BatchArgs {
     unsigned char* arena;
-    const BatchLattice* lat;
+    BatchLattice* lat;             // per-lattice t and parity advance on the device
     const BatchItem* items;
     uint32_t n_items;
-    uint32_t k;                    // full steps per launch
-    unsigned long long burn_in;    // steps t < burn_in are not added to the statistics
     BatchState* state;
     long long* stats;              // n_lattices x kStatFields
     long long* last_obs;           // n_lattices x 5
@@ -154,18 +155,10 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
     __shared__ uint32_t qbuf[BLOCK / 32][kBatchQueueFields][kQueueCap];
     __shared__ long long red[kNumObs][BLOCK / 32];
     __shared__ uint32_t item_sh;
-    __shared__ unsigned long long t0_sh, parity_sh;
+    __shared__ unsigned long long t0_sh, burn_sh;
+    __shared__ uint32_t par_sh, k_sh;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     uint32_t (*q)[kQueueCap] = qbuf[warp];
-    if (tid == 0) {
-        const volatile BatchState* vs = a.state;
-        t0_sh = vs->t;
-        parity_sh = vs->launches & 1ull;
-    }
-    __syncthreads();
-    const unsigned long long t0 = t0_sh;
-    const uint32_t par = (uint32_t)parity_sh;
-    const uint32_t k = a.k;
 
     for (;;) {
         if (tid == 0) item_sh = atomicAdd(&a.state->next, 1u);
@@ -173,7 +166,19 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         const uint32_t ii = item_sh;
         if (ii >= a.n_items) break;
         const BatchItem it = a.items[ii];
-        const BatchLattice* B = a.lat + it.lattice;
+        BatchLattice* B = a.lat + it.lattice;
+        // The lattice's counters change only when its last tile of this launch
+        // folds, after every tile of it (this one included) has read them.
+        if (tid == 0) {
+            const volatile BatchLattice* vb = B;
+            t0_sh = vb->t;
+            burn_sh = vb->burn_in;
+            par_sh = vb->parity;
+            k_sh = vb->k_this;
+        }
+        __syncthreads();
+        const unsigned long long t0 = t0_sh;
+        const uint32_t par = par_sh, k = k_sh;
         const uint32_t L = B->L, Wr = B->Wr, H = B->tile_rows;
         const uint32_t r0 = it.tile * H;
         const uint32_t Hloc = min(H, L - r0);
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
                 for (uint32_t j = 0; j < k; ++j) {
                     volatile long long* pj = partial + j * kNumObs;
                     const long long M = pj[0], Mt = pj[1], Sq = pj[2], SJ = pj[3], C = pj[4];
-                    if (t0 + j >= a.burn_in) {
+                    if (t0 + j >= burn_sh) {
                         st[0] += M;
                         st[1] += M * M;
                         st[2] += M < 0 ? -M : M;
@@ -280,6 +285,9 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
                     for (int f = 0; f < kNumObs; ++f) pj[f] = 0;
                 }
                 *ticket = 0u;
+                volatile BatchLattice* vb = B;
+                vb->t = t0 + k;
+                vb->parity = par ^ 1u;
                 __threadfence();
             }
         }
@@ -292,7 +300,6 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         if (d + 1 == gridDim.x) {
             a.state->next = 0u;
             a.state->done = 0u;
-            a.state->t += k;
             a.state->launches += 1ull;
             __threadfence();
         }
@@ -317,17 +324,17 @@ struct shk_batch {
     size_t off_state = 0, off_lat = 0, off_items = 0, off_stats = 0, off_last = 0;
     size_t items_capacity = 0;
     uint32_t n_items = 0;
+    // host mirror of the per-lattice counters (all lattices advance together)
+    uint64_t step = 0;
+    uint32_t parity = 0;
+    uint64_t burn_in = 0;
     // configuration
-    uint64_t step = 0;        // host copy of the step counter
     int k = 8;
     int block = 256;
     int tile_sites = 1 << 18;
-    bool dirty = true;        // descriptors / items must be re-uploaded
     size_t smem_bytes = 0;
     // graph of one launch
     cudaGraphExec_t graph = nullptr;
-    uint64_t graph_burn_in = ~0ull;
-    int graph_k = 0;
     std::string err;
 };
 
@@ -424,14 +431,12 @@ cudaError_t prepare_batch(shk_batch* b, int* grid) {
     }
 }
 
-cudaError_t launch_batch(shk_batch* b, int grid, uint64_t burn_in, cudaStream_t st) {
+cudaError_t launch_batch(shk_batch* b, int grid, cudaStream_t st) {
     BatchArgs args;
     args.arena = b->dev;
-    args.lat = reinterpret_cast<const BatchLattice*>(b->dev + b->off_lat);
+    args.lat = reinterpret_cast<BatchLattice*>(b->dev + b->off_lat);
     args.items = reinterpret_cast<const BatchItem*>(b->dev + b->off_items);
     args.n_items = b->n_items;
-    args.k = (uint32_t)b->k;
-    args.burn_in = burn_in;
     args.state = reinterpret_cast<BatchState*>(b->dev + b->off_state);
     args.stats = reinterpret_cast<long long*>(b->dev + b->off_stats);
     args.last_obs = reinterpret_cast<long long*>(b->dev + b->off_last);
@@ -443,20 +448,29 @@ cudaError_t launch_batch(shk_batch* b, int grid, uint64_t burn_in, cudaStream_t 
     return cudaGetLastError();
 }
 
-int upload_descriptors(shk_batch* b) {
+// Writes the descriptors (with the host mirror of t, parity, k and burn-in)
+// and, with rebuild, the work items; a rebuild drops the captured graph.
+int upload_descriptors(shk_batch* b, bool rebuild) {
     std::vector<BatchItem> items;
-    build_items(b, &items);
-    if (items.size() > b->items_capacity) return bfail(b, SHK_EINVAL, "shk_batch: too many tiles");
-    b->n_items = (uint32_t)items.size();
+    if (rebuild) {
+        build_items(b, &items);
+        if (items.size() > b->items_capacity) return bfail(b, SHK_EINVAL, "shk_batch: too many tiles");
+        b->n_items = (uint32_t)items.size();
+    }
+    for (BatchLattice& B : b->lat) {
+        B.t = b->step;
+        B.parity = b->parity;
+        B.k_this = (uint32_t)b->k;
+        B.burn_in = b->burn_in;
+    }
     cudaError_t e = cudaMemcpyAsync(b->dev + b->off_lat, b->lat.data(), b->lat.size() * sizeof(BatchLattice),
                                     cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && rebuild)
         e = cudaMemcpyAsync(b->dev + b->off_items, items.data(), items.size() * sizeof(BatchItem),
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch upload: %s", cudaGetErrorString(e));
-    b->dirty = false;
-    if (b->graph) {
+    if (rebuild && b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
     }
@@ -535,7 +549,7 @@ int shk_batch_create(int n, const int* L, const double* q, const double* J, cons
         delete b;
         return bfail(nullptr, SHK_ECUDA, "shk_batch_create: %s", cudaGetErrorString(e));
     }
-    const int rc = upload_descriptors(b);
+    const int rc = upload_descriptors(b, true);
     if (rc != SHK_OK) {
         delete b;
         return rc;
@@ -562,7 +576,7 @@ int shk_batch_configure(shk_batch* b, int steps_per_launch, int block_threads, i
     b->k = steps_per_launch;
     b->block = block_threads;
     b->tile_sites = tile_sites;
-    const int rc = upload_descriptors(b);
+    const int rc = upload_descriptors(b, true);
     if (rc != SHK_OK) return rc;
     // refuse a tile that does not fit in shared memory
     int dev = 0, optin = 0;
@@ -586,12 +600,15 @@ int shk_batch_init(shk_batch* b, int kind, uint64_t init_seed) {
         if (rc2 != SHK_OK) return bfail(b, rc2, "shk_batch_init: %s", shk_last_error(nullptr));
     }
     // state, statistics and last observables back to zero; sigma in buffer 0
+    b->step = 0;
+    b->parity = 0;
+    const int rc = upload_descriptors(b, false);
+    if (rc != SHK_OK) return rc;
     cudaError_t e = cudaMemsetAsync(b->dev + b->off_state, 0, 256, b->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(b->dev + b->off_stats, 0, (size_t)b->n * kStatFields * 8, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->dev + b->off_last, 0, (size_t)b->n * kNumObs * 8, b->stream);
     if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_init: %s", cudaGetErrorString(e));
-    b->step = 0;
     return SHK_OK;
 }
 
@@ -603,16 +620,13 @@ int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
     if (n_steps % (uint64_t)b->k != 0)
         return bfail(b, SHK_EINVAL, "shk_batch_run: n_steps=%llu is not a multiple of steps_per_launch=%d",
                      (unsigned long long)n_steps, b->k);
-    if (b->dirty) {
-        const int rc = upload_descriptors(b);
+    if (burn_in != b->burn_in) {
+        b->burn_in = burn_in;
+        const int rc = upload_descriptors(b, false);
         if (rc != SHK_OK) return rc;
     }
     cudaError_t e;
-    if (b->graph == nullptr || b->graph_burn_in != burn_in || b->graph_k != b->k) {
-        if (b->graph) {
-            cudaGraphExecDestroy(b->graph);
-            b->graph = nullptr;
-        }
+    if (b->graph == nullptr) {
         int grid = 0;
         e = prepare_batch(b, &grid);
         if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run: %s", cudaGetErrorString(e));
@@ -622,7 +636,7 @@ int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t le = launch_batch(b, grid, burn_in, cap);
+            const cudaError_t le = launch_batch(b, grid, cap);
             e = cudaStreamEndCapture(cap, &g);
             if (le != cudaSuccess) e = le;
         }
@@ -630,13 +644,12 @@ int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
         if (g) cudaGraphDestroy(g);
         cudaStreamDestroy(cap);
         if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run graph: %s", cudaGetErrorString(e));
-        b->graph_burn_in = burn_in;
-        b->graph_k = b->k;
     }
     for (uint64_t s = 0; s < n_steps; s += (uint64_t)b->k) {
         e = cudaGraphLaunch(b->graph, b->stream);
         if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run launch: %s", cudaGetErrorString(e));
         b->step += (uint64_t)b->k;
+        b->parity ^= 1u;
     }
     return SHK_OK;
 }
@@ -661,29 +674,445 @@ int shk_batch_read_observables(shk_batch* b, int64_t* host_obs) {
 
 int shk_batch_get_step(shk_batch* b, uint64_t* step) {
     if (!b || !step) return bfail(b, SHK_EINVAL, "shk_batch_get_step: NULL argument");
-    BatchState s;
-    cudaError_t e = cudaMemcpyAsync(&s, b->dev + b->off_state, sizeof s, cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_get_step: %s", cudaGetErrorString(e));
-    *step = s.t;
+    *step = b->step;
     return SHK_OK;
 }
 
 int shk_batch_read_spins(shk_batch* b, int idx, int plane, int8_t* host_out) {
     if (!b || !host_out || idx < 0 || idx >= b->n || (plane != 0 && plane != 1))
         return bfail(b, SHK_EINVAL, "shk_batch_read_spins: bad argument");
-    BatchState s;
-    cudaError_t e = cudaMemcpyAsync(&s, b->dev + b->off_state, sizeof s, cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_read_spins: %s", cudaGetErrorString(e));
     const BatchLattice& B = b->lat[idx];
-    const size_t off = plane == 0 ? B.sigma_off[s.launches & 1ull] : B.tau_off;
+    const size_t off = plane == 0 ? B.sigma_off[b->parity] : B.tau_off;
+    cudaError_t e;
     const int64_t N = (int64_t)B.L * B.L;
     std::vector<uint32_t> words((size_t)(N / 32));
     e = cudaMemcpyAsync(words.data(), b->dev + off, words.size() * 4, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_read_spins: %s", cudaGetErrorString(e));
     for (int64_t u = 0; u < N; ++u) host_out[u] = ((words[u >> 5] >> (u & 31)) & 1u) ? 1 : -1;
+    return SHK_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================
+// Serving: continuous batching of simulation jobs over the batch kernel.
+//
+// Jobs wait in a FIFO queue.  At every tick the scheduler (1) admits queued
+// jobs, oldest first, while a slot is free and the job's planes fit in the
+// HBM budget (first-fit allocation in the caller's arena), initialising their
+// lattices on the device; (2) advances every active job by min(slice,
+// remaining) steps in one launch of the persistent kernel, each job's lattice,
+// step counter and random-number key staying resident; (3) retires finished
+// jobs, copying their exact statistics, last observables and a hash of the
+// final sigma.  Jobs admitted at a tick share that tick's launch with jobs
+// already running, so work of different jobs overlaps on the device, and a
+// job's result does not depend on what else runs (its random numbers depend
+// only on its own seed, lattice id and step).
+// ======================================================================
+
+#include <deque>
+#include <map>
+
+namespace {
+
+constexpr uint32_t kMaxTilesPerJob = 512;
+constexpr int kMaxServerL = 8192;
+
+struct Slot {
+    bool used = false;
+    uint64_t job_id = 0;
+    shk_job job{};
+    uint64_t remaining = 0;
+    size_t mem_off = 0, mem_bytes = 0;
+    uint64_t submit_tick = 0, admit_tick = 0;
+};
+
+struct Pending {
+    uint64_t job_id;
+    shk_job job;
+    uint64_t submit_tick;
+};
+
+// First-fit allocator over [0, capacity) with coalescing of freed ranges.
+class Arena {
+public:
+    void reset(size_t capacity) {
+        free_.clear();
+        if (capacity) free_[0] = capacity;
+    }
+    bool alloc(size_t n, size_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const size_t rest = it->second - n;
+                const size_t start = it->first + n;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        auto it = free_.emplace(off, n).first;
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+private:
+    std::map<size_t, size_t> free_;
+};
+
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+struct shk_server {
+    int max_slots = 0;
+    size_t budget = 0, used = 0;
+    unsigned char* dev = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    size_t off_state = 0, off_lat = 0, off_items = 0, off_stats = 0, off_last = 0, off_arena = 0;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::vector<BatchLattice> lat;
+    std::deque<Pending> pending;
+    std::vector<shk_result> done;
+    size_t max_pending = 1u << 20;
+    uint64_t next_id = 1;
+    uint64_t tick = 0;
+    int k = 16;
+    int block = 256;
+    int tile_sites = 1 << 17;
+    size_t smem_attr = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_server_err;
+
+int sfail(shk_server* s, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    else g_server_err = buf;
+    set_thread_error(buf);
+    return code;
+}
+
+size_t job_bytes(int L) {
+    Geometry g;
+    make_geometry(L, kBitpack, &g);
+    return 3 * g.plane_bytes + kScratchPerLattice;
+}
+
+void server_layout(int max_slots, size_t* off_state, size_t* off_lat, size_t* off_items, size_t* off_stats,
+                   size_t* off_last, size_t* off_arena) {
+    size_t off = 0;
+    *off_state = off;
+    off += 256;
+    *off_lat = off;
+    off = align256(off + (size_t)max_slots * sizeof(BatchLattice));
+    *off_items = off;
+    off = align256(off + (size_t)max_slots * kMaxTilesPerJob * sizeof(BatchItem));
+    *off_stats = off;
+    off = align256(off + (size_t)max_slots * kStatFields * 8);
+    *off_last = off;
+    off = align256(off + (size_t)max_slots * kNumObs * 8);
+    *off_arena = off;
+}
+
+void retire(shk_server* s, int i, int status, bool fetch) {
+    Slot& sl = s->slots[i];
+    shk_result r;
+    std::memset(&r, 0, sizeof r);
+    r.job_id = sl.job_id;
+    r.status = status;
+    r.steps_done = sl.job.n_steps - sl.remaining;
+    r.submit_tick = sl.submit_tick;
+    r.admit_tick = sl.admit_tick;
+    r.done_tick = s->tick;
+    if (fetch) {
+        const BatchLattice& B = s->lat[i];
+        cudaMemcpyAsync(r.stats, s->dev + s->off_stats + (size_t)i * kStatFields * 8, kStatFields * 8,
+                        cudaMemcpyDeviceToHost, s->stream);
+        cudaMemcpyAsync(r.last_obs, s->dev + s->off_last + (size_t)i * kNumObs * 8, kNumObs * 8,
+                        cudaMemcpyDeviceToHost, s->stream);
+        std::vector<unsigned char> sig((size_t)B.L * B.L / 8);
+        cudaMemcpyAsync(sig.data(), s->dev + B.sigma_off[B.parity], sig.size(), cudaMemcpyDeviceToHost, s->stream);
+        cudaStreamSynchronize(s->stream);
+        r.sigma_hash = fnv1a64(sig.data(), sig.size());
+    }
+    s->done.push_back(r);
+    s->arena.release(sl.mem_off, sl.mem_bytes);
+    s->used -= sl.mem_bytes;
+    sl = Slot();
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t shk_server_bytes(int max_slots, size_t arena_bytes) {
+    if (max_slots <= 0) return 0;
+    size_t a, b, c, d, e, f;
+    server_layout(max_slots, &a, &b, &c, &d, &e, &f);
+    return f + arena_bytes;
+}
+
+int shk_server_create(int max_slots, size_t hbm_budget, void* dev_mem, size_t bytes, void* stream,
+                      shk_server** out) {
+    if (!out) return sfail(nullptr, SHK_EINVAL, "shk_server_create: out is NULL");
+    *out = nullptr;
+    if (max_slots <= 0 || max_slots > 65536)
+        return sfail(nullptr, SHK_EINVAL, "shk_server_create: max_slots must be in 1..65536");
+    if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) & 255u))
+        return sfail(nullptr, SHK_EINVAL, "shk_server_create: dev_mem must be non-NULL and 256-byte aligned");
+    shk_server* s = new (std::nothrow) shk_server();
+    if (!s) return sfail(nullptr, SHK_ENOMEM, "shk_server_create: host allocation failed");
+    server_layout(max_slots, &s->off_state, &s->off_lat, &s->off_items, &s->off_stats, &s->off_last,
+                  &s->off_arena);
+    if (bytes < s->off_arena + 4096) {
+        const size_t need = s->off_arena + 4096;
+        delete s;
+        return sfail(nullptr, SHK_ENOMEM, "shk_server_create: %zu bytes given, at least %zu needed", bytes, need);
+    }
+    s->max_slots = max_slots;
+    s->dev = static_cast<unsigned char*>(dev_mem);
+    s->bytes = bytes;
+    s->budget = hbm_budget;
+    s->stream = static_cast<cudaStream_t>(stream);
+    s->arena.reset(bytes - s->off_arena);
+    s->slots.resize(max_slots);
+    s->lat.resize(max_slots);
+    std::memset(s->lat.data(), 0, s->lat.size() * sizeof(BatchLattice));
+    cudaError_t e = cudaMemsetAsync(s->dev, 0, s->off_arena, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        delete s;
+        return sfail(nullptr, SHK_ECUDA, "shk_server_create: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return SHK_OK;
+}
+
+void shk_server_destroy(shk_server* s) { delete s; }
+
+const char* shk_server_last_error(const shk_server* s) { return s ? s->err.c_str() : g_server_err.c_str(); }
+
+int shk_server_configure(shk_server* s, int steps_per_tick, int block_threads, int tile_sites, size_t max_pending) {
+    if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_configure: NULL handle");
+    if (steps_per_tick < 1 || steps_per_tick > kMaxStepsPerLaunch)
+        return sfail(s, SHK_EINVAL, "shk_server_configure: steps_per_tick must be in 1..%d", kMaxStepsPerLaunch);
+    if (block_threads != 128 && block_threads != 256 && block_threads != 512)
+        return sfail(s, SHK_EINVAL, "shk_server_configure: block_threads must be 128, 256 or 512");
+    if (tile_sites < 1024) return sfail(s, SHK_EINVAL, "shk_server_configure: tile_sites must be >= 1024");
+    if (max_pending < 1) return sfail(s, SHK_EINVAL, "shk_server_configure: max_pending must be >= 1");
+    s->k = steps_per_tick;
+    s->block = block_threads;
+    s->tile_sites = tile_sites;
+    s->max_pending = max_pending;
+    return SHK_OK;
+}
+
+int shk_server_submit(shk_server* s, const shk_job* job, uint64_t* job_id) {
+    if (!s || !job) return sfail(s, SHK_EINVAL, "shk_server_submit: NULL argument");
+    if (job->L < 32 || job->L > kMaxServerL || job->L % 32 != 0)
+        return sfail(s, SHK_EINVAL, "shk_server_submit: L=%d (need 32 <= L <= %d, L %% 32 == 0)", job->L, kMaxServerL);
+    if (!std::isfinite(job->q) || !std::isfinite(job->J))
+        return sfail(s, SHK_EINVAL, "shk_server_submit: q and J must be finite");
+    if (job->n_steps < 1 || job->n_steps >= SHK_MAX_STEP)
+        return sfail(s, SHK_EINVAL, "shk_server_submit: n_steps must be in 1..2^31-1");
+    if (job->init_kind != SHK_INIT_ALL_UP && job->init_kind != SHK_INIT_ALL_DOWN && job->init_kind != SHK_INIT_RANDOM)
+        return sfail(s, SHK_EINVAL, "shk_server_submit: unknown init_kind %d", job->init_kind);
+    if (job_bytes(job->L) > s->budget)
+        return sfail(s, SHK_EINVAL, "shk_server_submit: a lattice of side %d needs %zu bytes, more than the HBM budget",
+                     job->L, job_bytes(job->L));
+    if (s->pending.size() >= s->max_pending) return sfail(s, SHK_EBUSY, "shk_server_submit: queue full");
+    const uint64_t id = s->next_id++;
+    s->pending.push_back({id, *job, s->tick});
+    if (job_id) *job_id = id;
+    return SHK_OK;
+}
+
+int shk_server_cancel(shk_server* s, uint64_t job_id) {
+    if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_cancel: NULL handle");
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if (it->job_id == job_id) {
+            shk_result r;
+            std::memset(&r, 0, sizeof r);
+            r.job_id = job_id;
+            r.status = SHK_ECANCELLED;
+            r.submit_tick = it->submit_tick;
+            r.done_tick = s->tick;
+            s->done.push_back(r);
+            s->pending.erase(it);
+            return SHK_OK;
+        }
+    }
+    for (int i = 0; i < s->max_slots; ++i) {
+        if (s->slots[i].used && s->slots[i].job_id == job_id) {
+            retire(s, i, SHK_ECANCELLED, false);
+            return SHK_OK;
+        }
+    }
+    return sfail(s, SHK_EINVAL, "shk_server_cancel: no queued or running job %llu", (unsigned long long)job_id);
+}
+
+int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
+    if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_tick: NULL handle");
+    cudaError_t e = cudaSuccess;
+    // (1) admission, oldest first, while a slot is free and the job fits
+    while (!s->pending.empty()) {
+        const Pending& p = s->pending.front();
+        int slot = -1;
+        for (int i = 0; i < s->max_slots; ++i)
+            if (!s->slots[i].used) {
+                slot = i;
+                break;
+            }
+        if (slot < 0) break;
+        const size_t need = job_bytes(p.job.L);
+        if (s->used + need > s->budget) break;
+        size_t off = 0;
+        if (!s->arena.alloc(need, &off)) break;
+        Slot& sl = s->slots[slot];
+        sl.used = true;
+        sl.job_id = p.job_id;
+        sl.job = p.job;
+        sl.remaining = p.job.n_steps;
+        sl.mem_off = off;
+        sl.mem_bytes = need;
+        sl.submit_tick = p.submit_tick;
+        sl.admit_tick = s->tick;
+        s->used += need;
+        Geometry g;
+        make_geometry(p.job.L, kBitpack, &g);
+        BatchLattice& B = s->lat[slot];
+        std::memset(&B, 0, sizeof B);
+        B.L = (uint32_t)p.job.L;
+        B.Wr = g.Wr;
+        const size_t base = s->off_arena + off;
+        B.sigma_off[0] = base;
+        B.sigma_off[1] = base + g.plane_bytes;
+        B.tau_off = base + 2 * g.plane_bytes;
+        B.scratch_off = base + 3 * g.plane_bytes;
+        B.burn_in = p.job.burn_in;
+        uint32_t T[6];
+        host_thresholds(p.job.q, p.job.J, T);
+        make_draw_params(p.job.seed, p.job.lattice_id, T, 0u, &B.P);
+        const uint32_t H = (uint32_t)std::max<int64_t>(
+            std::max<int64_t>(1, (B.L + kMaxTilesPerJob - 1) / kMaxTilesPerJob),
+            std::min<int64_t>(B.L, s->tile_sites / (int64_t)B.L));
+        B.tile_rows = std::min<uint32_t>(H, B.L);
+        B.ntiles = (B.L + B.tile_rows - 1) / B.tile_rows;
+        if (shk_init_plane(SHK_BITPACK, s->dev + B.sigma_off[0], B.L, p.job.init_kind, p.job.init_seed,
+                           p.job.lattice_id, 0, s->stream) != SHK_OK ||
+            shk_init_plane(SHK_BITPACK, s->dev + B.tau_off, B.L, p.job.init_kind, p.job.init_seed,
+                           p.job.lattice_id, 1, s->stream) != SHK_OK)
+            return sfail(s, SHK_ECUDA, "shk_server_tick: init: %s", shk_last_error(nullptr));
+        e = cudaMemsetAsync(s->dev + B.scratch_off, 0, kScratchPerLattice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(s->dev + s->off_stats + (size_t)slot * kStatFields * 8, 0, kStatFields * 8, s->stream);
+        if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_tick: %s", cudaGetErrorString(e));
+        s->pending.pop_front();
+    }
+    // (2) one launch advancing every active job
+    std::vector<BatchItem> items;
+    size_t smem_words = 0;
+    for (int i = 0; i < s->max_slots; ++i) {
+        Slot& sl = s->slots[i];
+        if (!sl.used) continue;
+        BatchLattice& B = s->lat[i];
+        B.k_this = (uint32_t)std::min<uint64_t>((uint64_t)s->k, sl.remaining);
+        for (uint32_t t = 0; t < B.ntiles; ++t) items.push_back({(uint32_t)i, t});
+        const uint32_t rows = B.ntiles == 1 ? B.L : B.tile_rows + 2 * B.k_this + 1;
+        smem_words = std::max<size_t>(smem_words, 2 * (size_t)rows * B.Wr);
+    }
+    if (!items.empty()) {
+        std::stable_sort(items.begin(), items.end(), [&](const BatchItem& x, const BatchItem& y) {
+            const BatchLattice& A = s->lat[x.lattice];
+            const BatchLattice& C = s->lat[y.lattice];
+            return (uint64_t)A.tile_rows * A.L > (uint64_t)C.tile_rows * C.L;
+        });
+        e = cudaMemcpyAsync(s->dev + s->off_lat, s->lat.data(), s->lat.size() * sizeof(BatchLattice),
+                            cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(s->dev + s->off_items, items.data(), items.size() * sizeof(BatchItem),
+                                cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_tick upload: %s", cudaGetErrorString(e));
+        // reuse the batch launcher through a temporary view
+        shk_batch view;
+        view.dev = s->dev;
+        view.off_state = s->off_state;
+        view.off_lat = s->off_lat;
+        view.off_items = s->off_items;
+        view.off_stats = s->off_stats;
+        view.off_last = s->off_last;
+        view.n_items = (uint32_t)items.size();
+        view.block = s->block;
+        view.smem_bytes = smem_words * 4;
+        int grid = 0;
+        e = prepare_batch(&view, &grid);
+        if (e == cudaSuccess) e = launch_batch(&view, grid, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_tick launch: %s", cudaGetErrorString(e));
+        // (3) advance the host mirror; retire finished jobs
+        for (int i = 0; i < s->max_slots; ++i) {
+            Slot& sl = s->slots[i];
+            if (!sl.used) continue;
+            BatchLattice& B = s->lat[i];
+            B.t += B.k_this;
+            B.parity ^= 1u;
+            sl.remaining -= B.k_this;
+        }
+        s->tick += 1;
+        for (int i = 0; i < s->max_slots; ++i)
+            if (s->slots[i].used && s->slots[i].remaining == 0) retire(s, i, SHK_OK, true);
+    }
+    int active = 0;
+    for (const Slot& sl : s->slots) active += sl.used ? 1 : 0;
+    if (n_active) *n_active = active;
+    if (n_pending) *n_pending = (int)s->pending.size();
+    return SHK_OK;
+}
+
+int shk_server_poll(shk_server* s, shk_result* out, int max, int* n_out) {
+    if (!s || (!out && max > 0) || !n_out) return sfail(s, SHK_EINVAL, "shk_server_poll: bad argument");
+    const int n = std::min<int>(max, (int)s->done.size());
+    for (int i = 0; i < n; ++i) out[i] = s->done[i];
+    s->done.erase(s->done.begin(), s->done.begin() + n);
+    *n_out = n;
+    return SHK_OK;
+}
+
+int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes) {
+    if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_stats: NULL handle");
+    if (tick) *tick = s->tick;
+    if (used_bytes) *used_bytes = s->used;
     return SHK_OK;
 }
 

@@ -1,0 +1,112 @@
+"""Serving with continuous batching: jobs admitted at different ticks share
+launches, yet each job's result (exact statistics, last observables, hash of
+the final sigma) is the same alone, in the mix, and as a single-lattice run."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1908_07341_gb300 as shk
+from paper_1908_07341_gb300.batch import stats_from_observables
+from paper_1908_07341_gb300.serve import Server, fnv1a64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1908_07341_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+JOBS = [dict(L=64, q=1.0, J=0.25, seed=1, lattice_id=0, n_steps=37, burn_in=10),
+        dict(L=128, q=0.5, J=0.5, seed=2, lattice_id=1, n_steps=16, burn_in=0),
+        dict(L=32, q=3.0, J=0.44, seed=3, lattice_id=2, n_steps=5, burn_in=2),
+        dict(L=256, q=0.6585, J=0.6585, seed=4, lattice_id=3, n_steps=50, burn_in=25),
+        dict(L=96, q=0.05, J=1.7, seed=5, lattice_id=4, n_steps=23, burn_in=0, init="up"),
+        dict(L=512, q=1.2, J=0.3, seed=6, lattice_id=5, n_steps=19, burn_in=9),
+        dict(L=160, q=0.8, J=0.6, seed=2 ** 40 + 7, lattice_id=6, n_steps=64, burn_in=63),
+        dict(L=64, q=2.0, J=0.1, seed=8, lattice_id=7, n_steps=1, burn_in=0, init="down")]
+
+
+def _single(job):
+    lat = shk.Lattice(job["L"], "bitpack").set_seed(job["seed"], job["lattice_id"])
+    lat.set_params(job["q"], job["J"]).init(job.get("init", "random"), init_seed=job.get("init_seed", 0))
+    obs = lat.run(job["n_steps"], obs=True).cpu().numpy()
+    raw = lat.plane(0)[: job["L"] * job["L"] // 8].cpu().numpy().tobytes()
+    return stats_from_observables(obs[job["burn_in"]:]), obs[-1], fnv1a64(raw)
+
+
+def _run_all(server, jobs, arrive_at_tick):
+    ids, results, tick = {}, {}, 0
+    while len(results) < len(jobs):
+        for i, j in enumerate(jobs):
+            if arrive_at_tick[i] == tick:
+                ids[server.submit(**j)] = i
+        server.tick()
+        for r in server.poll():
+            results[ids[r["job_id"]]] = r
+        tick += 1
+        assert tick < 10_000
+    return [results[i] for i in range(len(jobs))]
+
+
+@pytest.mark.parametrize("k", [1, 8, 16])
+def test_each_job_same_alone_and_in_the_mix(k):
+    mixed = Server(max_slots=16, arena_bytes=64 << 20).configure(steps_per_tick=k)
+    res_mix = _run_all(mixed, JOBS, [0, 0, 1, 1, 2, 3, 3, 5])
+    for i, j in enumerate(JOBS):
+        alone = Server(max_slots=2, arena_bytes=8 << 20).configure(steps_per_tick=k)
+        (r_alone,) = _run_all(alone, [j], [0])
+        want_stats, want_last, want_hash = _single(j)
+        for r in (res_mix[i], r_alone):
+            assert r["status"] == 0 and r["steps_done"] == j["n_steps"]
+            assert np.array_equal(r["stats"], want_stats), i
+            assert np.array_equal(r["last_obs"], want_last), i
+            assert r["sigma_hash"] == want_hash, i
+
+
+def test_admission_waits_for_memory_and_results_do_not_change():
+    # a 110 kB budget: the 512^2 job (three 32 kB planes and its scratch) must
+    # wait until the jobs admitted before it have finished
+    srv = Server(max_slots=16, arena_bytes=64 << 20, hbm_budget=110_000).configure(steps_per_tick=8)
+    ids = [srv.submit(**j) for j in JOBS]
+    saw_waiting = False
+    results = {}
+    for _ in range(10_000):
+        active, pending = srv.tick()
+        saw_waiting |= pending > 0 and active > 0
+        assert srv.stats()["used_bytes"] <= 110_000
+        for r in srv.poll():
+            results[r["job_id"]] = r
+        if len(results) == len(JOBS):
+            break
+    assert saw_waiting
+    for jid, j in zip(ids, JOBS):
+        want_stats, want_last, want_hash = _single(j)
+        assert np.array_equal(results[jid]["stats"], want_stats)
+        assert results[jid]["sigma_hash"] == want_hash
+
+
+def test_queue_limit_cancel_and_validation():
+    srv = Server(max_slots=1, arena_bytes=8 << 20).configure(steps_per_tick=4, max_pending=2)
+    a = srv.submit(**JOBS[3])
+    b = srv.submit(**JOBS[0])
+    with pytest.raises(shk.ShakenError) as e:
+        srv.submit(**JOBS[1])
+    assert e.value.status == -5                       # SHK_EBUSY, never blocks
+    srv.tick()                                        # a admitted, b waits
+    srv.cancel(b)                                     # cancel a queued job
+    srv.tick()
+    srv.cancel(a)                                     # cancel a running job
+    got = {r["job_id"]: r for r in srv.poll()}
+    assert got[a]["status"] == -7 and got[b]["status"] == -7
+    assert 0 < got[a]["steps_done"] < JOBS[3]["n_steps"]
+    with pytest.raises(shk.ShakenError):
+        srv.submit(L=33, q=1.0, J=0.3, seed=1, lattice_id=0, n_steps=5)
+    with pytest.raises(shk.ShakenError):
+        srv.submit(L=64, q=float("nan"), J=0.3, seed=1, lattice_id=0, n_steps=5)
+    with pytest.raises(shk.ShakenError):
+        srv.cancel(12345)
+    assert srv.tick() == (0, 0)
