@@ -363,6 +363,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if not args.no_batched:
         line["batched"] = bench_batched(dev, stream)
+    if not args.no_serving:
+        line["serving"] = bench_serving(dev, stream, n_jobs=args.serving_jobs)
     if world == 1 and not args.no_cpu_baseline:
         rows = 8192
         rate, secs, units = _oracle_sample_rate(rows)
@@ -433,6 +435,38 @@ def bench_batched(dev, stream, plain_steps: int = 100):
             "launches": w["steps"] // tuned["best"][0]}
 
 
+def bench_serving(dev, stream, n_jobs: int = 200, steps_per_tick: int = 32):
+    """Continuous batching on a slice of the serving stream: the first n_jobs
+    jobs of the Poisson stream (mean 200 arrivals/s, L log-uniform in
+    [64, 4096], steps log-uniform in [10^3, 10^5]) replayed in real time,
+    then two sub-saturation replays at about 50% and 80% of the measured
+    capacity.  Latency = end of the tick that finished a job - its arrival."""
+    from paper_1908_07341_gb300 import workloads
+    from paper_1908_07341_gb300.serve import Server, replay_stream
+
+    def one(n, rate, seed=5):
+        w = workloads.serving_stream(n_jobs=n, rate_per_s=rate, seed=seed)
+        srv = Server(max_slots=1024, arena_bytes=8 << 30, hbm_budget=96 << 30, device=dev, stream=stream)
+        srv.configure(steps_per_tick=steps_per_tick, block_threads=256, tile_sites=1 << 17)
+        r = replay_stream(srv, w["jobs"], w["arrivals"])
+        srv.close()
+        assert all(x["status"] == 0 for x in r["results"])
+        return {"jobs": n, "arrival_rate_per_s": rate, "site_updates": w["site_updates"],
+                "wall_s": r["wall_s"], "throughput": w["site_updates"] / r["wall_s"],
+                "p50_latency_s": r["p50_s"], "p99_latency_s": r["p99_s"], "mean_latency_s": r["mean_s"]}
+
+    sat = one(n_jobs, 200.0)
+    mean_work = sat["site_updates"] / n_jobs
+    capacity_jobs_per_s = sat["throughput"] / mean_work
+    sub = [one(max(20, n_jobs // 4), round(f * capacity_jobs_per_s, 2), seed=6 + i)
+           for i, f in enumerate((0.5, 0.8))]
+    return {"workload": f"first {n_jobs} jobs of the serving stream (Poisson 200/s, L log-uniform [64,4096], "
+                        "q~U[0.05,3], J~U[0.05,1.5], steps log-uniform [1e3,1e5], seed 5, admission cap 96 GB)",
+            "unit": UNIT, "value": sat["throughput"], "p50_latency_s": sat["p50_latency_s"],
+            "p99_latency_s": sat["p99_latency_s"], "saturated": sat, "sub_saturation": sub,
+            "steps_per_tick": steps_per_tick, "capacity_jobs_per_s": capacity_jobs_per_s}
+
+
 def run_kernel_case(spec: str) -> int:
     """--kernel-case LAYOUT:L:LAUNCHES -- a random-start lattice and LAUNCHES
     alternating half-step launches through shk_halfstep (the benchmark's
@@ -492,6 +526,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched phase-diagram line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving line")
+    ap.add_argument("--serving-jobs", type=int, default=200,
+                    help="jobs of the serving stream to replay (10000 = the full stream)")
     ap.add_argument("--kernel-case", default=None,
                     help="LAYOUT:L:LAUNCHES -- only run half-step launches (for profiling)")
     args = ap.parse_args()
