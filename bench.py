@@ -435,7 +435,7 @@ def bench_batched(dev, stream, plain_steps: int = 100):
             "launches": w["steps"] // tuned["best"][0]}
 
 
-def bench_serving(dev, stream, n_jobs: int = 200, steps_per_tick: int = 32):
+def bench_serving(dev, stream, n_jobs: int = 200, steps_per_launch: int = 2, launches_per_tick: int = 16):
     """Continuous batching on a slice of the serving stream: the first n_jobs
     jobs of the Poisson stream (mean 200 arrivals/s, L log-uniform in
     [64, 4096], steps log-uniform in [10^3, 10^5]) replayed in real time,
@@ -447,7 +447,8 @@ def bench_serving(dev, stream, n_jobs: int = 200, steps_per_tick: int = 32):
     def one(n, rate, seed=5):
         w = workloads.serving_stream(n_jobs=n, rate_per_s=rate, seed=seed)
         srv = Server(max_slots=1024, arena_bytes=8 << 30, hbm_budget=96 << 30, device=dev, stream=stream)
-        srv.configure(steps_per_tick=steps_per_tick, block_threads=256, tile_sites=1 << 17)
+        srv.configure(steps_per_launch=steps_per_launch, launches_per_tick=launches_per_tick, block_threads=256,
+                      tile_sites=1 << 18)
         r = replay_stream(srv, w["jobs"], w["arrivals"])
         srv.close()
         assert all(x["status"] == 0 for x in r["results"])
@@ -464,7 +465,8 @@ def bench_serving(dev, stream, n_jobs: int = 200, steps_per_tick: int = 32):
                         "q~U[0.05,3], J~U[0.05,1.5], steps log-uniform [1e3,1e5], seed 5, admission cap 96 GB)",
             "unit": UNIT, "value": sat["throughput"], "p50_latency_s": sat["p50_latency_s"],
             "p99_latency_s": sat["p99_latency_s"], "saturated": sat, "sub_saturation": sub,
-            "steps_per_tick": steps_per_tick, "capacity_jobs_per_s": capacity_jobs_per_s}
+            "steps_per_launch": steps_per_launch, "launches_per_tick": launches_per_tick,
+            "capacity_jobs_per_s": capacity_jobs_per_s}
 
 
 def run_kernel_case(spec: str) -> int:

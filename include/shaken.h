@@ -312,9 +312,13 @@ int shk_server_create(int max_slots, size_t hbm_budget, void* dev_mem, size_t by
                       shk_server** out);
 void shk_server_destroy(shk_server* s);
 const char* shk_server_last_error(const shk_server* s);
-/* Defaults: 16 steps per tick, 256 threads, 2^17 sites per tile, 2^20 queued. */
-int shk_server_configure(shk_server* s, int steps_per_tick, int block_threads, int tile_sites,
-                         size_t max_pending);
+/* A tick enqueues launches_per_tick launches of steps_per_launch steps each
+ * (a job finishing part-way skips the rest) and waits for them.  Tiles hold
+ * at most tile_sites sites, fewer while little work is active.  Defaults: 2
+ * steps per launch, 16 launches per tick, 256 threads, 2^18 sites per tile,
+ * 2^20 queued jobs. */
+int shk_server_configure(shk_server* s, int steps_per_launch, int launches_per_tick, int block_threads,
+                         int tile_sites, size_t max_pending);
 int shk_server_submit(shk_server* s, const shk_job* job, uint64_t* job_id);
 int shk_server_cancel(shk_server* s, uint64_t job_id);
 int shk_server_tick(shk_server* s, int* n_active, int* n_pending);

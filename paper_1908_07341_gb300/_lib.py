@@ -70,7 +70,7 @@ SIGNATURES = {
     "shk_server_create": (_i, [_i, _sz, _vp, _sz, _vp, _vp]),
     "shk_server_destroy": (None, [_vp]),
     "shk_server_last_error": (_c.c_char_p, [_vp]),
-    "shk_server_configure": (_i, [_vp, _i, _i, _i, _sz]),
+    "shk_server_configure": (_i, [_vp, _i, _i, _i, _i, _sz]),
     "shk_server_submit": (_i, [_vp, _vp, _vp]),
     "shk_server_cancel": (_i, [_vp, _u64]),
     "shk_server_tick": (_i, [_vp, _vp, _vp]),

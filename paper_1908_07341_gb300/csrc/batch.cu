@@ -43,20 +43,21 @@ constexpr int kBatchQueueFields = 7;   // w, und, up, S, N1, N2, local index
 
 struct BatchLattice {
     uint32_t L, Wr;             // side, words per row
-    uint32_t tile_rows;         // H
-    uint32_t ntiles;
     unsigned long long sigma_off[2];   // byte offsets of the two sigma buffers
     unsigned long long tau_off;
     unsigned long long scratch_off;    // partials [kMaxStepsPerLaunch][5] int64, then the ticket
     unsigned long long t;              // next step of this lattice (advanced on the device)
+    unsigned long long remaining;      // steps still to run (decreased on the device)
     unsigned long long burn_in;        // steps t < burn_in are not added to the statistics
     uint32_t parity;                   // sigma buffer holding the current state (flipped on the device)
-    uint32_t k_this;                   // full steps this launch (1..kMaxStepsPerLaunch)
+    uint32_t pad;
     DrawParams P;
 };
 
+// One tile: rows [r0, r0 + nrows) of a lattice cut into ntiles tiles in this
+// launch (ntiles == 1: the whole torus, rows wrapping).
 struct BatchItem {
-    uint32_t lattice, tile;
+    uint32_t lattice, r0, nrows, ntiles;
 };
 
 struct BatchState {
@@ -67,9 +68,10 @@ struct BatchState {
 
 struct BatchArgs {
     unsigned char* arena;
-    BatchLattice* lat;             // per-lattice t and parity advance on the device
+    BatchLattice* lat;             // per-lattice t, parity and remaining advance on the device
     const BatchItem* items;
     uint32_t n_items;
+    uint32_t k;                    // full steps per launch (a lattice runs min(k, remaining))
     BatchState* state;
     long long* stats;              // n_lattices x kStatFields
     long long* last_obs;           // n_lattices x 5
@@ -174,17 +176,22 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
             t0_sh = vb->t;
             burn_sh = vb->burn_in;
             par_sh = vb->parity;
-            k_sh = vb->k_this;
+            const unsigned long long rem = vb->remaining;
+            k_sh = (uint32_t)(rem < a.k ? rem : a.k);
         }
         __syncthreads();
         const unsigned long long t0 = t0_sh;
         const uint32_t par = par_sh, k = k_sh;
-        const uint32_t L = B->L, Wr = B->Wr, H = B->tile_rows;
-        const uint32_t r0 = it.tile * H;
-        const uint32_t Hloc = min(H, L - r0);
+        if (k == 0) {              // the lattice has finished: nothing to do
+            __syncthreads();
+            continue;
+        }
+        const uint32_t L = B->L, Wr = B->Wr;
+        const uint32_t r0 = it.r0;
+        const uint32_t Hloc = it.nrows;
         // A lattice that is a single tile keeps its whole torus, rows wrapping;
         // otherwise the tile carries rows r0-k .. r0+Hloc+k (k below, k+1 above).
-        const bool wrap = B->ntiles == 1;
+        const bool wrap = it.ntiles == 1;
         const uint32_t R = wrap ? L : Hloc + 2 * k + 1;
         const int64_t r_base = wrap ? 0 : (int64_t)r0 - (int64_t)k;
         const uint32_t own_lo = wrap ? 0 : k;           // local rows of the tile itself
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
             __threadfence();
             unsigned int* ticket = reinterpret_cast<unsigned int*>(partial + kMaxStepsPerLaunch * kNumObs);
             const unsigned int tk = atomicAdd(ticket, 1u);
-            if (tk + 1 == B->ntiles) {
+            if (tk + 1 == it.ntiles) {
                 __threadfence();
                 long long* st = a.stats + (size_t)it.lattice * kStatFields;
                 for (uint32_t j = 0; j < k; ++j) {
@@ -288,6 +295,7 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
                 volatile BatchLattice* vb = B;
                 vb->t = t0 + k;
                 vb->parity = par ^ 1u;
+                vb->remaining = vb->remaining - k;
                 __threadfence();
             }
         }
@@ -386,26 +394,36 @@ bool batch_layout(int n, const int* L, std::vector<size_t>* lat_offsets, size_t*
     return true;
 }
 
+// Rows per tile of a lattice of side L for a target of tile_sites sites.
+uint32_t tile_rows_for(uint32_t L, int64_t tile_sites) {
+    return (uint32_t)std::max<int64_t>(1, std::min<int64_t>(L, tile_sites / (int64_t)L));
+}
+
+// Appends the tiles of lattice i (rows per tile H) and returns the shared
+// memory words its largest tile needs for k steps per launch.
+size_t add_tiles(std::vector<BatchItem>* items, uint32_t i, uint32_t L, uint32_t Wr, uint32_t H, uint32_t k) {
+    const uint32_t nt = (L + H - 1) / H;
+    for (uint32_t t = 0; t < nt; ++t) items->push_back({i, t * H, std::min(H, L - t * H), nt});
+    const uint32_t rows = nt == 1 ? L : H + 2 * k + 1;
+    return 2 * (size_t)rows * Wr;
+}
+
+void sort_items(std::vector<BatchItem>* items, const std::vector<BatchLattice>& lat) {
+    std::stable_sort(items->begin(), items->end(), [&](const BatchItem& x, const BatchItem& y) {
+        return (uint64_t)x.nrows * lat[x.lattice].L > (uint64_t)y.nrows * lat[y.lattice].L;
+    });
+}
+
 // Builds the work items (largest tiles first) and the shared memory a tile needs.
 void build_items(shk_batch* b, std::vector<BatchItem>* items) {
     items->clear();
     size_t smem_words = 0;
     for (int i = 0; i < b->n; ++i) {
-        BatchLattice& B = b->lat[i];
-        const uint32_t H = (uint32_t)std::max<int64_t>(1, std::min<int64_t>(B.L, b->tile_sites / (int64_t)B.L));
-        B.tile_rows = H;
-        B.ntiles = (B.L + H - 1) / H;
-        for (uint32_t t = 0; t < B.ntiles; ++t) items->push_back({(uint32_t)i, t});
-        const uint32_t rows = B.ntiles == 1 ? B.L : H + 2 * b->k + 1;
-        smem_words = std::max<size_t>(smem_words, 2 * (size_t)rows * B.Wr);
+        const BatchLattice& B = b->lat[i];
+        smem_words = std::max(smem_words, add_tiles(items, (uint32_t)i, B.L, B.Wr,
+                                                    tile_rows_for(B.L, b->tile_sites), (uint32_t)b->k));
     }
-    std::stable_sort(items->begin(), items->end(), [&](const BatchItem& x, const BatchItem& y) {
-        const BatchLattice& A = b->lat[x.lattice];
-        const BatchLattice& C = b->lat[y.lattice];
-        const uint64_t wx = (uint64_t)std::min(A.tile_rows, A.L - x.tile * A.tile_rows) * A.L;
-        const uint64_t wy = (uint64_t)std::min(C.tile_rows, C.L - y.tile * C.tile_rows) * C.L;
-        return wx > wy;
-    });
+    sort_items(items, b->lat);
     b->smem_bytes = smem_words * 4;
 }
 
@@ -437,6 +455,7 @@ cudaError_t launch_batch(shk_batch* b, int grid, cudaStream_t st) {
     args.lat = reinterpret_cast<BatchLattice*>(b->dev + b->off_lat);
     args.items = reinterpret_cast<const BatchItem*>(b->dev + b->off_items);
     args.n_items = b->n_items;
+    args.k = (uint32_t)b->k;
     args.state = reinterpret_cast<BatchState*>(b->dev + b->off_state);
     args.stats = reinterpret_cast<long long*>(b->dev + b->off_stats);
     args.last_obs = reinterpret_cast<long long*>(b->dev + b->off_last);
@@ -460,7 +479,7 @@ int upload_descriptors(shk_batch* b, bool rebuild) {
     for (BatchLattice& B : b->lat) {
         B.t = b->step;
         B.parity = b->parity;
-        B.k_this = (uint32_t)b->k;
+        B.remaining = ~0ull;              // a batch lattice never runs out of steps
         B.burn_in = b->burn_in;
     }
     cudaError_t e = cudaMemcpyAsync(b->dev + b->off_lat, b->lat.data(), b->lat.size() * sizeof(BatchLattice),
@@ -800,10 +819,10 @@ struct shk_server {
     size_t max_pending = 1u << 20;
     uint64_t next_id = 1;
     uint64_t tick = 0;
-    int k = 16;
+    int k = 2;                  // steps per launch
+    int launches = 16;          // launches per tick
     int block = 256;
-    int tile_sites = 1 << 17;
-    size_t smem_attr = 0;
+    int tile_sites = 1 << 18;   // largest tile; smaller while few jobs are active
     std::string err;
 };
 
@@ -923,15 +942,19 @@ void shk_server_destroy(shk_server* s) { delete s; }
 
 const char* shk_server_last_error(const shk_server* s) { return s ? s->err.c_str() : g_server_err.c_str(); }
 
-int shk_server_configure(shk_server* s, int steps_per_tick, int block_threads, int tile_sites, size_t max_pending) {
+int shk_server_configure(shk_server* s, int steps_per_launch, int launches_per_tick, int block_threads,
+                         int tile_sites, size_t max_pending) {
     if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_configure: NULL handle");
-    if (steps_per_tick < 1 || steps_per_tick > kMaxStepsPerLaunch)
-        return sfail(s, SHK_EINVAL, "shk_server_configure: steps_per_tick must be in 1..%d", kMaxStepsPerLaunch);
+    if (steps_per_launch < 1 || steps_per_launch > kMaxStepsPerLaunch)
+        return sfail(s, SHK_EINVAL, "shk_server_configure: steps_per_launch must be in 1..%d", kMaxStepsPerLaunch);
+    if (launches_per_tick < 1 || launches_per_tick > 4096)
+        return sfail(s, SHK_EINVAL, "shk_server_configure: launches_per_tick must be in 1..4096");
     if (block_threads != 128 && block_threads != 256 && block_threads != 512)
         return sfail(s, SHK_EINVAL, "shk_server_configure: block_threads must be 128, 256 or 512");
     if (tile_sites < 1024) return sfail(s, SHK_EINVAL, "shk_server_configure: tile_sites must be >= 1024");
     if (max_pending < 1) return sfail(s, SHK_EINVAL, "shk_server_configure: max_pending must be >= 1");
-    s->k = steps_per_tick;
+    s->k = steps_per_launch;
+    s->launches = launches_per_tick;
     s->block = block_threads;
     s->tile_sites = tile_sites;
     s->max_pending = max_pending;
@@ -1020,15 +1043,13 @@ int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
         B.sigma_off[1] = base + g.plane_bytes;
         B.tau_off = base + 2 * g.plane_bytes;
         B.scratch_off = base + 3 * g.plane_bytes;
+        B.t = 0;
+        B.remaining = p.job.n_steps;
         B.burn_in = p.job.burn_in;
+        B.parity = 0;
         uint32_t T[6];
         host_thresholds(p.job.q, p.job.J, T);
         make_draw_params(p.job.seed, p.job.lattice_id, T, 0u, &B.P);
-        const uint32_t H = (uint32_t)std::max<int64_t>(
-            std::max<int64_t>(1, (B.L + kMaxTilesPerJob - 1) / kMaxTilesPerJob),
-            std::min<int64_t>(B.L, s->tile_sites / (int64_t)B.L));
-        B.tile_rows = std::min<uint32_t>(H, B.L);
-        B.ntiles = (B.L + B.tile_rows - 1) / B.tile_rows;
         if (shk_init_plane(SHK_BITPACK, s->dev + B.sigma_off[0], B.L, p.job.init_kind, p.job.init_seed,
                            p.job.lattice_id, 0, s->stream) != SHK_OK ||
             shk_init_plane(SHK_BITPACK, s->dev + B.tau_off, B.L, p.job.init_kind, p.job.init_seed,
@@ -1037,34 +1058,35 @@ int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
         e = cudaMemsetAsync(s->dev + B.scratch_off, 0, kScratchPerLattice, s->stream);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(s->dev + s->off_stats + (size_t)slot * kStatFields * 8, 0, kStatFields * 8, s->stream);
+        if (e == cudaSuccess)   // the device copy of the descriptor is authoritative from here on
+            e = cudaMemcpyAsync(s->dev + s->off_lat + (size_t)slot * sizeof(BatchLattice), &B, sizeof B,
+                                cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_tick: %s", cudaGetErrorString(e));
         s->pending.pop_front();
     }
-    // (2) one launch advancing every active job
+    // (2) tiles of every active job, smaller while little work is active so
+    // that the launch still spreads over the GPU
+    uint64_t active_sites = 0;
+    for (int i = 0; i < s->max_slots; ++i)
+        if (s->slots[i].used) active_sites += (uint64_t)s->lat[i].L * s->lat[i].L;
+    const int64_t target_items = 4 * (int64_t)sm_count() * 2;
+    const int64_t tile_sites = std::max<int64_t>(
+        4096, std::min<int64_t>(s->tile_sites, (int64_t)(active_sites / (uint64_t)std::max<int64_t>(1, target_items))));
     std::vector<BatchItem> items;
     size_t smem_words = 0;
     for (int i = 0; i < s->max_slots; ++i) {
-        Slot& sl = s->slots[i];
-        if (!sl.used) continue;
-        BatchLattice& B = s->lat[i];
-        B.k_this = (uint32_t)std::min<uint64_t>((uint64_t)s->k, sl.remaining);
-        for (uint32_t t = 0; t < B.ntiles; ++t) items.push_back({(uint32_t)i, t});
-        const uint32_t rows = B.ntiles == 1 ? B.L : B.tile_rows + 2 * B.k_this + 1;
-        smem_words = std::max<size_t>(smem_words, 2 * (size_t)rows * B.Wr);
+        if (!s->slots[i].used) continue;
+        const BatchLattice& B = s->lat[i];
+        uint32_t H = tile_rows_for(B.L, tile_sites);
+        H = std::max<uint32_t>(H, (B.L + kMaxTilesPerJob - 1) / kMaxTilesPerJob);
+        smem_words = std::max(smem_words, add_tiles(&items, (uint32_t)i, B.L, B.Wr, H, (uint32_t)s->k));
     }
     if (!items.empty()) {
-        std::stable_sort(items.begin(), items.end(), [&](const BatchItem& x, const BatchItem& y) {
-            const BatchLattice& A = s->lat[x.lattice];
-            const BatchLattice& C = s->lat[y.lattice];
-            return (uint64_t)A.tile_rows * A.L > (uint64_t)C.tile_rows * C.L;
-        });
-        e = cudaMemcpyAsync(s->dev + s->off_lat, s->lat.data(), s->lat.size() * sizeof(BatchLattice),
+        sort_items(&items, s->lat);
+        e = cudaMemcpyAsync(s->dev + s->off_items, items.data(), items.size() * sizeof(BatchItem),
                             cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->dev + s->off_items, items.data(), items.size() * sizeof(BatchItem),
-                                cudaMemcpyHostToDevice, s->stream);
         if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_tick upload: %s", cudaGetErrorString(e));
-        // reuse the batch launcher through a temporary view
+        // reuse the batch launcher through a view of the server's tables
         shk_batch view;
         view.dev = s->dev;
         view.off_state = s->off_state;
@@ -1074,20 +1096,27 @@ int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
         view.off_last = s->off_last;
         view.n_items = (uint32_t)items.size();
         view.block = s->block;
+        view.k = s->k;
         view.smem_bytes = smem_words * 4;
         int grid = 0;
         e = prepare_batch(&view, &grid);
-        if (e == cudaSuccess) e = launch_batch(&view, grid, s->stream);
+        // several launches per tick: a job that finishes part-way skips its
+        // tiles in the remaining launches (the kernel reads its remaining steps)
+        for (int l = 0; e == cudaSuccess && l < s->launches; ++l) e = launch_batch(&view, grid, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_tick launch: %s", cudaGetErrorString(e));
-        // (3) advance the host mirror; retire finished jobs
+        // (3) host mirror of what the launches did; retire finished jobs
+        const uint64_t k = (uint64_t)s->k, per_tick = k * (uint64_t)s->launches;
         for (int i = 0; i < s->max_slots; ++i) {
             Slot& sl = s->slots[i];
             if (!sl.used) continue;
             BatchLattice& B = s->lat[i];
-            B.t += B.k_this;
-            B.parity ^= 1u;
-            sl.remaining -= B.k_this;
+            const uint64_t adv = std::min<uint64_t>(sl.remaining, per_tick);
+            const uint64_t nl = (adv + k - 1) / k;           // launches that did work
+            B.t += adv;
+            B.remaining -= adv;
+            B.parity ^= (uint32_t)(nl & 1u);
+            sl.remaining -= adv;
         }
         s->tick += 1;
         for (int i = 0; i < s->max_slots; ++i)

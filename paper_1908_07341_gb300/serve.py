@@ -73,9 +73,10 @@ class Server:
         except Exception:
             pass
 
-    def configure(self, steps_per_tick=16, block_threads=256, tile_sites=1 << 17, max_pending=1 << 20):
-        _check(lib().shk_server_configure(self._h, int(steps_per_tick), int(block_threads), int(tile_sites),
-                                          int(max_pending)), self._h)
+    def configure(self, steps_per_launch=2, launches_per_tick=16, block_threads=256, tile_sites=1 << 18,
+                  max_pending=1 << 20):
+        _check(lib().shk_server_configure(self._h, int(steps_per_launch), int(launches_per_tick),
+                                          int(block_threads), int(tile_sites), int(max_pending)), self._h)
         return self
 
     def submit(self, L, q, J, seed, lattice_id, n_steps, burn_in=0, init="random", init_seed=0) -> int:

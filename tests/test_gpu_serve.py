@@ -52,12 +52,12 @@ def _run_all(server, jobs, arrive_at_tick):
     return [results[i] for i in range(len(jobs))]
 
 
-@pytest.mark.parametrize("k", [1, 8, 16])
-def test_each_job_same_alone_and_in_the_mix(k):
-    mixed = Server(max_slots=16, arena_bytes=64 << 20).configure(steps_per_tick=k)
+@pytest.mark.parametrize("k,launches", [(1, 1), (2, 4), (3, 5), (8, 2)])
+def test_each_job_same_alone_and_in_the_mix(k, launches):
+    mixed = Server(max_slots=16, arena_bytes=64 << 20).configure(steps_per_launch=k, launches_per_tick=launches)
     res_mix = _run_all(mixed, JOBS, [0, 0, 1, 1, 2, 3, 3, 5])
     for i, j in enumerate(JOBS):
-        alone = Server(max_slots=2, arena_bytes=8 << 20).configure(steps_per_tick=k)
+        alone = Server(max_slots=2, arena_bytes=8 << 20).configure(steps_per_launch=k, launches_per_tick=launches)
         (r_alone,) = _run_all(alone, [j], [0])
         want_stats, want_last, want_hash = _single(j)
         for r in (res_mix[i], r_alone):
@@ -70,7 +70,8 @@ def test_each_job_same_alone_and_in_the_mix(k):
 def test_admission_waits_for_memory_and_results_do_not_change():
     # a 110 kB budget: the 512^2 job (three 32 kB planes and its scratch) must
     # wait until the jobs admitted before it have finished
-    srv = Server(max_slots=16, arena_bytes=64 << 20, hbm_budget=110_000).configure(steps_per_tick=8)
+    srv = Server(max_slots=16, arena_bytes=64 << 20, hbm_budget=110_000).configure(steps_per_launch=2,
+                                                                                  launches_per_tick=4)
     ids = [srv.submit(**j) for j in JOBS]
     saw_waiting = False
     results = {}
@@ -90,7 +91,8 @@ def test_admission_waits_for_memory_and_results_do_not_change():
 
 
 def test_queue_limit_cancel_and_validation():
-    srv = Server(max_slots=1, arena_bytes=8 << 20).configure(steps_per_tick=4, max_pending=2)
+    srv = Server(max_slots=1, arena_bytes=8 << 20).configure(steps_per_launch=2, launches_per_tick=2,
+                                                             max_pending=2)
     a = srv.submit(**JOBS[3])
     b = srv.submit(**JOBS[0])
     with pytest.raises(shk.ShakenError) as e:
