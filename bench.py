@@ -356,7 +356,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                  "roofline": {"bound": "hbm", "achieved": hbm_bytes_i8 / (kern8_ms / 1e3) / 1e9,
                               "peak": hbm_gbs, "unit": "GB/s",
                               "frac": hbm_bytes_i8 / (kern8_ms / 1e3) / 1e9 / hbm_gbs,
-                              "traffic": traffic.get("k_sweep_i8"), "kernel_ms": kern8_ms,
+                              "traffic": traffic.get("k_sweep_strip_int8"), "kernel_ms": kern8_ms,
                               "peak_kind": peak_kind}},
         "clocks": clocks,
         "wall_s_bitpack": wall,
@@ -482,6 +482,8 @@ def run_kernel_case(spec: str) -> int:
 
     layout, side, launches = spec.split(":")
     side, launches = int(side), int(launches)
+    from paper_1908_07341_gb300 import tune
+    tune.autotune(layout, side)                  # the launch shape the benchmark uses
     lat = shk.Lattice(side, layout).set_seed(SEED, 0).set_params(Q, J).init("random", init_seed=INIT_SEED)
     T = shk.thresholds(Q, J)
     acc = torch.zeros(shk.NOBS, dtype=torch.int64, device="cuda")
@@ -494,11 +496,32 @@ def run_kernel_case(spec: str) -> int:
     return 0
 
 
+def run_batch_case(n_lattices: int) -> int:
+    """--batch-case N -- the first N lattices of the phase-diagram workload,
+    autotuned, then 8 launches: the command profiled for k_batch."""
+    import torch
+
+    from paper_1908_07341_gb300 import build as libbuild
+
+    libbuild.build()
+    from paper_1908_07341_gb300 import tune, workloads
+    from paper_1908_07341_gb300.batch import Batch
+
+    w = workloads.phase_diagram_batch()
+    sel = {k: w[k][:n_lattices] for k in ("L", "q", "J", "seed", "lattice_id")}
+    b = Batch(**sel)
+    best = tune.autotune_batch(b, init_kind="random", init_seed=w["init_seed"])["best"]
+    b.run(8 * best[0])
+    torch.cuda.synchronize()
+    print(json.dumps({"batch_case": n_lattices, "tuned": list(best), "step": b.step}))
+    return 0
+
+
 def _kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("device.cuh", "kernels.cu"):
+    for f in ("device.cuh", "kernels.cu", "batch.cu"):
         with open(os.path.join(ROOT, "paper_1908_07341_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -531,11 +554,15 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving line")
     ap.add_argument("--serving-jobs", type=int, default=200,
                     help="jobs of the serving stream to replay (10000 = the full stream)")
+    ap.add_argument("--batch-case", type=int, default=0,
+                    help="N -- only run the first N phase-diagram lattices (for profiling)")
     ap.add_argument("--kernel-case", default=None,
                     help="LAYOUT:L:LAUNCHES -- only run half-step launches (for profiling)")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args.kernel_case)
+    if args.batch_case:
+        return run_batch_case(args.batch_case)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     world = int(os.environ.get("WORLD_SIZE", "1"))
