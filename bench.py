@@ -47,6 +47,29 @@ SM_COUNT = 152
 MAX_SM_MHZ = 2070.0
 
 
+def replica_lattice_id(rank: int) -> int:
+    """Replicas only: rank r advances its own lattice with lattice id r (the
+    third Philox counter word), so the ranks' random streams never overlap and
+    no data crosses between ranks."""
+    return int(rank)
+
+
+def whole_job_rate(local_ms: float, units_per_rank: float, dist=None, device=None) -> tuple[float, float]:
+    """Whole-job throughput: the units all ranks processed divided by the
+    slowest rank's time (a MAX all-reduce of the per-rank milliseconds).
+    Returns (rate per second, max milliseconds)."""
+    import torch
+
+    world = 1
+    ms = float(local_ms)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_rank / (ms / 1e3), ms
+
+
 def _peaks():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -225,7 +248,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         from paper_1908_07341_gb300 import tune
         tune.autotune(layout, L)                 # launch shape for this size (untimed)
         lat = shk.Lattice(L, layout, device=dev, stream=stream)
-        lat.set_seed(SEED, rank).set_params(Q, J).init("random", init_seed=INIT_SEED)
+        lat.set_seed(SEED, replica_lattice_id(rank)).set_params(Q, J).init("random", init_seed=INIT_SEED)
         obs = torch.empty((STEPS_PER_BENCH_STEP, shk.NOBS), dtype=torch.int64, device=dev)
         for _ in range(warmup):
             lat.run(STEPS_PER_BENCH_STEP, obs)
@@ -299,23 +322,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     wall = time.perf_counter() - t_wall0
     clocks = sampler.stop(tuple(window)) if sampler else None
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms = max_over_ranks(ms)
     units_per_step = 2 * L * L * STEPS_PER_BENCH_STEP
-    value = world * units_per_step * args.steps / (ms / 1e3)
-    e2e_ms = max_over_ranks(e2e["ms"])
-    e2e_value = world * units_per_step * e2e["steps"] / (e2e_ms / 1e3)
+    value, ms = whole_job_rate(ms, units_per_step * args.steps, dist, dev)
+    e2e_value, _ = whole_job_rate(e2e["ms"], units_per_step * e2e["steps"], dist, dev)
 
     # secondary line: the int8 layout on the same workload (fewer steps)
     ms8, _, kern8_ms = bench_layout("int8", max(2, args.steps // 5), 1, with_e2e=False)
-    ms8 = max_over_ranks(ms8)
-    value8 = world * units_per_step * max(2, args.steps // 5) / (ms8 / 1e3)
+    value8, _ = whole_job_rate(ms8, units_per_step * max(2, args.steps // 5), dist, dev)
 
     if rank != 0:
         if dist is not None:

@@ -246,6 +246,28 @@ __device__ __forceinline__ void unpack32(uint32_t bits, uint4& lo, uint4& hi) {
     hi.w = unpack4(bits >> 28);
 }
 
+// ---------------------------------------------------------------- async copies
+
+// Asynchronous global -> shared copies (cp.async, sm_80 and later): the copy
+// holds no registers and completes in the background; cp.async.wait_group N
+// returns once at most N committed groups of this thread are still pending.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ---------------------------------------------------------------- division
 
 // Division by a fixed divisor d >= 1 for n < 2^31: q = (umulhi(n, m) + n) >> s

@@ -342,9 +342,9 @@ __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uin
 }
 
 // Continues the `count` (<= 32) oldest parked blocks; all lanes call it.
-template <int HALF, int LAYOUT>
-__device__ __forceinline__ void drain_queue(const SweepArgs& a, uint32_t (*q)[kQueueCap], uint32_t head,
-                                            int count, bool cnn, int (&acc)[3]) {
+template <int HALF, int LAYOUT, class PP>
+__device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, uint32_t (*q)[kQueueCap],
+                                            uint32_t head, int count, bool cnn, int (&acc)[3]) {
     const uint32_t lane = threadIdx.x & 31;
     const bool has = (int)lane < count;
     const uint32_t i = (head + lane) & (kQueueCap - 1);
@@ -358,13 +358,14 @@ __device__ __forceinline__ void drain_queue(const SweepArgs& a, uint32_t (*q)[kQ
         N2 = q[5][i];
     }
     const BlockClass k = block_class(S, N1, N2);
-    const uint32_t res = draw_rest(k, w, und, up, a.hs, a.P);
+    const uint32_t res = draw_rest(k, w, und, up, a.hs, P);
     if (has) finish_block<HALF, LAYOUT>(a, w, res, S, N1, N2, cnn, acc);
 }
 
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    const DrawParams& P = a.P;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
@@ -388,7 +389,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
         }
         const BlockClass k = block_class(S, N1, N2);
         uint32_t und, up;
-        draw_first_two(k, w, 0xffffffffu, a.hs, a.P, und, up);
+        draw_first_two(k, w, 0xffffffffu, a.hs, P, und, up);
         const bool parked = und != 0u;
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
         count += __popc(mask);
         if (count >= 32) {
             __syncwarp();
-            drain_queue<HALF, LAYOUT>(a, q, head, 32, cnn, acc);
+            drain_queue<HALF, LAYOUT>(a, P, q, head, 32, cnn, acc);
             __syncwarp();
             head = (head + 32) & (kQueueCap - 1);
             count -= 32;
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     }
     if (count > 0) {
         __syncwarp();
-        drain_queue<HALF, LAYOUT>(a, q, head, count, cnn, acc);
+        drain_queue<HALF, LAYOUT>(a, P, q, head, count, cnn, acc);
     }
     finish_step<HALF>(acc, a);
 }
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    const DrawParams& P = a.P;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
     int acc[3] = {0, 0, 0};
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
             count += __popc(mask);
             if (count >= 32) {
                 __syncwarp();
-                drain_queue<HALF, LAYOUT>(a, q, head, 32, cnn, acc);
+                drain_queue<HALF, LAYOUT>(a, P, q, head, 32, cnn, acc);
                 __syncwarp();
                 head = (head + 32) & (kQueueCap - 1);
                 count -= 32;
@@ -564,7 +566,147 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
     }
     if (count > 0) {
         __syncwarp();
-        drain_queue<HALF, LAYOUT>(a, q, head, count, cnn, acc);
+        drain_queue<HALF, LAYOUT>(a, P, q, head, count, cnn, acc);
+    }
+    finish_step<HALF>(acc, a);
+}
+
+// Strip walk with the rows staged DEPTH rows ahead into a per-warp ring in
+// shared memory by cp.async (each lane copies its own block's word or 32
+// bytes, lane 0 / 31 also the strip-edge word); otherwise as k_sweep_strip.
+template <int LAYOUT>
+struct RowWords {
+    static constexpr int kWords = LAYOUT == kBitpack ? 1 : 8;   // 32-bit words per lane per row
+};
+
+template <int HALF, int LAYOUT, int BLOCK, int MINB, int DEPTH>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepArgs a) {
+    constexpr int NW = RowWords<LAYOUT>::kWords;
+    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    const DrawParams& P = a.P;
+    __shared__ __align__(16) uint32_t ring[BLOCK / 32][DEPTH][32 * NW];
+    __shared__ __align__(16) uint32_t ring_edge[BLOCK / 32][DEPTH][4];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t (*q)[kQueueCap] = qbuf[wib];
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    uint32_t head = 0;
+    int count = 0;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t W = a.Wr, L = a.L;
+    const uint32_t nstrips = W / 32;
+    const bool edge_lane = HALF == 0 ? lane == 0 : lane == 31;
+    const uint64_t total = (uint64_t)nstrips * L;
+    uint64_t pos = total * gwarp / nwarps;
+    const uint64_t end = total * (gwarp + 1) / nwarps;
+    while (pos < end) {
+        const uint32_t strip = (uint32_t)(pos / L);
+        const uint32_t r0 = (uint32_t)(pos - (uint64_t)strip * L);
+        const uint64_t left_here = end - pos, left_in_strip = L - r0;
+        const uint32_t nrows = (uint32_t)(left_here < left_in_strip ? left_here : left_in_strip);
+        pos += nrows;
+        const uint32_t col = strip * 32 + lane;
+        const uint32_t edge_block = HALF == 0 ? (strip == 0 ? W - 1 : strip * 32 - 1)
+                                              : (strip + 1 == nstrips ? 0 : strip * 32 + 32);
+        auto row_at = [&](uint32_t i) -> uint32_t { return HALF == 0 ? r0 + i : r0 + nrows - 1 - i; };
+        // stage row i of the walk into ring slot i % DEPTH (always commit a group)
+        auto stage = [&](uint32_t i) {
+            if (i < nrows) {
+                const uint32_t r = row_at(i);
+                const size_t b = (size_t)r * W + col;
+                uint32_t* dst = &ring[wib][i % DEPTH][lane * NW];
+                if constexpr (LAYOUT == kBitpack) {
+                    cp_async4(dst, static_cast<const uint32_t*>(a.src) + b);
+                } else {
+                    const int8_t* g = static_cast<const int8_t*>(a.src) + 32 * b;
+                    cp_async16(dst, g);
+                    cp_async16(dst + 4, g + 16);
+                }
+                if (edge_lane) {
+                    const size_t eb = (size_t)r * W + edge_block;
+                    if constexpr (LAYOUT == kBitpack) {
+                        cp_async4(&ring_edge[wib][i % DEPTH][0], static_cast<const uint32_t*>(a.src) + eb);
+                    } else {
+                        // the 4-byte word holding the byte next to the strip
+                        const int8_t* g = static_cast<const int8_t*>(a.src) + 32 * eb + (HALF == 0 ? 28 : 0);
+                        cp_async4(&ring_edge[wib][i % DEPTH][0], g);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        const uint32_t first = row_at(0);
+        const uint32_t nb_row = HALF == 0 ? (first == 0 ? L - 1 : first - 1) : (first + 1 == L ? 0 : first + 1);
+        uint32_t prev = row_bits<LAYOUT>(load_row<LAYOUT>(a.src, nb_row * W + col));
+        __syncwarp();
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) stage(d);
+        for (uint32_t i = 0; i < nrows; ++i) {
+            const uint32_t row = row_at(i);
+            cp_async_wait<DEPTH - 1>();      // row i has landed (this lane's copies)
+            __syncwarp();                    // ... and every other lane's
+            const uint32_t* slot = &ring[wib][i % DEPTH][lane * NW];
+            uint32_t S;
+            if constexpr (LAYOUT == kBitpack) {
+                S = slot[0];
+            } else {
+                const uint4 lo = *reinterpret_cast<const uint4*>(slot);
+                const uint4 hi = *reinterpret_cast<const uint4*>(slot + 4);
+                S = pack_up32(lo, hi);
+            }
+            uint32_t edge = 0;
+            if (edge_lane) {
+                const uint32_t e = ring_edge[wib][i % DEPTH][0];
+                if constexpr (LAYOUT == kBitpack) edge = HALF == 0 ? e >> 31 : e & 1u;
+                else edge = HALF == 0 ? (uint32_t)((int8_t)(e >> 24) > 0) : (uint32_t)((int8_t)(e & 0xFFu) > 0);
+            }
+            __syncwarp();                    // everyone has read the slot before it is refilled
+            stage(i + DEPTH);
+            const uint32_t N1 = prev;
+            uint32_t N2;
+            if (HALF == 0) {
+                const uint32_t left = __shfl_up_sync(0xffffffffu, S, 1) >> 31;
+                N2 = (S << 1) | (lane == 0 ? edge : left);
+            } else {
+                const uint32_t right = __shfl_down_sync(0xffffffffu, S, 1) & 1u;
+                N2 = (S >> 1) | ((lane == 31 ? edge : right) << 31);
+            }
+            const uint32_t w = row * W + col;
+            const BlockClass k = block_class(S, N1, N2);
+            uint32_t und, up;
+            draw_first_two(k, w, 0xffffffffu, a.hs, P, und, up);
+            const bool parked = und != 0u;
+            const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+            if (parked) {
+                const uint32_t qi = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+                q[0][qi] = w;
+                q[1][qi] = und;
+                q[2][qi] = up;
+                q[3][qi] = S;
+                q[4][qi] = N1;
+                q[5][qi] = N2;
+            } else {
+                finish_block<HALF, LAYOUT>(a, w, up, S, N1, N2, cnn, acc);
+            }
+            count += __popc(mask);
+            if (count >= 32) {
+                __syncwarp();
+                drain_queue<HALF, LAYOUT>(a, P, q, head, 32, cnn, acc);
+                __syncwarp();
+                head = (head + 32) & (kQueueCap - 1);
+                count -= 32;
+            }
+            prev = S;
+        }
+        cp_async_wait<0>();                  // no copy may still target the ring
+        __syncwarp();
+    }
+    if (count > 0) {
+        __syncwarp();
+        drain_queue<HALF, LAYOUT>(a, P, q, head, count, cnn, acc);
     }
     finish_step<HALF>(acc, a);
 }
@@ -871,36 +1013,35 @@ using SweepKernel = void (*)(SweepArgs);
 struct SweepVariant {
     SweepKernel k[2];   // half A, half B
     int block;
+    bool strip;         // needs rows of a multiple of 32 blocks (L % 1024 == 0)
     const char* name;
 };
 
+// The first entry of each table is the default (the fastest measured at
+// L = 16384 on GB300); the autotuner may pick another per size.
 static const SweepVariant kBpVariants[] = {
-    {{k_sweep_strip<0, kBitpack, 256, 3>, k_sweep_strip<1, kBitpack, 256, 3>}, 256, "strip-256x3"},
-    {{k_sweep_strip<0, kBitpack, 128, 6>, k_sweep_strip<1, kBitpack, 128, 6>}, 128, "strip-128x6"},
-    {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, "queue-256x3"},
-    {{k_sweep_q<0, kBitpack, 256, 4>, k_sweep_q<1, kBitpack, 256, 4>}, 256, "queue-256x4"},
-    {{k_sweep_q<0, kBitpack, 128, 6>, k_sweep_q<1, kBitpack, 128, 6>}, 128, "queue-128x6"},
-    {{k_sweep_bp<0, 1, true, 256, 4>, k_sweep_bp<1, 1, true, 256, 4>}, 256, "ilp1-prefetch-256x4"},
-    {{k_sweep_bp<0, 2, true, 256, 2>, k_sweep_bp<1, 2, true, 256, 2>}, 256, "ilp2-prefetch-256x2"},
-    {{k_sweep_bp<0, 1, false, 256, 1>, k_sweep_bp<1, 1, false, 256, 1>}, 256, "ilp1-256"},
-    {{k_sweep_bp<0, 1, true, 128, 8>, k_sweep_bp<1, 1, true, 128, 8>}, 128, "ilp1-prefetch-128x8"},
-    {{k_sweep_bp<0, 2, true, 128, 4>, k_sweep_bp<1, 2, true, 128, 4>}, 128, "ilp2-prefetch-128x4"},
+    {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, false, "queue-256x3"},
+    {{k_sweep_strip_async<0, kBitpack, 256, 3, 4>, k_sweep_strip_async<1, kBitpack, 256, 3, 4>}, 256, true,
+     "strip-async4-256x3"},
+    {{k_sweep_strip<0, kBitpack, 256, 3>, k_sweep_strip<1, kBitpack, 256, 3>}, 256, true, "strip-256x3"},
+    {{k_sweep_q<0, kBitpack, 128, 6>, k_sweep_q<1, kBitpack, 128, 6>}, 128, false, "queue-128x6"},
+    {{k_sweep_q<0, kBitpack, 256, 4>, k_sweep_q<1, kBitpack, 256, 4>}, 256, false, "queue-256x4"},
+    {{k_sweep_bp<0, 1, false, 256, 1>, k_sweep_bp<1, 1, false, 256, 1>}, 256, false, "plain-256"},
 };
 
 static const SweepVariant kI8Variants[] = {
-    {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, "strip-256x3"},
-    {{k_sweep_strip<0, kInt8, 128, 6>, k_sweep_strip<1, kInt8, 128, 6>}, 128, "strip-128x6"},
-    {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, "queue-256x3"},
-    {{k_sweep_q<0, kInt8, 256, 4>, k_sweep_q<1, kInt8, 256, 4>}, 256, "queue-256x4"},
-    {{k_sweep_i8a<0, true, 256, 4>, k_sweep_i8a<1, true, 256, 4>}, 256, "prefetch-256x4"},
-    {{k_sweep_i8a<0, true, 256, 3>, k_sweep_i8a<1, true, 256, 3>}, 256, "prefetch-256x3"},
-    {{k_sweep_i8a<0, false, 256, 1>, k_sweep_i8a<1, false, 256, 1>}, 256, "plain-256"},
-    {{k_sweep_i8a<0, true, 128, 8>, k_sweep_i8a<1, true, 128, 8>}, 128, "prefetch-128x8"},
+    {{k_sweep_strip_async<0, kInt8, 256, 3, 2>, k_sweep_strip_async<1, kInt8, 256, 3, 2>}, 256, true,
+     "strip-async2-256x3"},
+    {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, true, "strip-256x3"},
+    {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, false, "queue-256x3"},
+    {{k_sweep_q<0, kInt8, 256, 4>, k_sweep_q<1, kInt8, 256, 4>}, 256, false, "queue-256x4"},
+    {{k_sweep_i8a<0, false, 256, 1>, k_sweep_i8a<1, false, 256, 1>}, 256, false, "plain-256"},
 };
 
 constexpr int kNumBpVariants = sizeof(kBpVariants) / sizeof(kBpVariants[0]);
-constexpr int kNumStripVariants = 2;   // the first entries of both tables
 constexpr int kNumI8Variants = sizeof(kI8Variants) / sizeof(kI8Variants[0]);
+constexpr int kBpRowFallback = 0;   // non-strip variant used when rows are too short
+constexpr int kI8RowFallback = 2;
 
 static std::atomic<int> g_bp_variant{0};
 static std::atomic<int> g_i8_variant{0};
@@ -929,10 +1070,11 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
                             long long* obs_prev, long long* zero_slot, cudaStream_t st) {
     SweepArgs a = sweep_args(g, src, dst, P, hs, obs_cur, half == 0 ? obs_prev : nullptr, zero_slot);
     if (g.layout == kBitpack || g.aligned) {
+        const SweepVariant* table = g.layout == kBitpack ? kBpVariants : kI8Variants;
         int vi = g.layout == kBitpack ? g_bp_variant.load() : g_i8_variant.load();
         // strip-walk variants need rows of a multiple of 32 blocks (L % 1024 == 0)
-        if (vi < kNumStripVariants && (g.Wr % 32) != 0) vi = kNumStripVariants;
-        const SweepVariant& v = g.layout == kBitpack ? kBpVariants[vi] : kI8Variants[vi];
+        if (table[vi].strip && (g.Wr % 32) != 0) vi = g.layout == kBitpack ? kBpRowFallback : kI8RowFallback;
+        const SweepVariant& v = table[vi];
         SweepKernel k = v.k[half];
         const int grid = grid_for(k, v.block, g.nblocks);
         k<<<grid, v.block, 0, st>>>(a);
