@@ -162,6 +162,28 @@ int shk_set_sweep_variant(int layout, int variant);
 int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
                    uint32_t lattice_id, uint32_t plane_index, void* stream);
 
+/* Diagonal spin-spin sums of one bit-packed plane (Section 3.3, Table 1):
+ *   out[k]          += sum_x s_x s_{x + (l_k, l_k)}     (SW-NE: (0,0) with (l,l))
+ *   out[n_lags + k] += sum_x s_x s_{x + (l_k, -l_k)}    (NW-SE: (0,l) with (l,0))
+ * over all x = (i, j) of the torus (translation average times L^2).
+ * plane: device bit-packed plane (L % 32 == 0); lags: host array of n_lags
+ * (1..8) lags in [0, L); out: device int64[2 n_lags], ADDED to (caller
+ * zeroes it).  Asynchronous. */
+int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags, int64_t* out, void* stream);
+
+/* Coalescence times (Section 3.2): for each pair, two copies of the chain
+ * on an L x L torus (32 <= L <= 256, L % 32 == 0), one from all +1 and one
+ * from all -1, driven by the same random numbers (seed, lattice id, steps).
+ * The dynamics preserves the order, so they sandwich every other start, and
+ * once the sigma planes agree they agree forever.  host_T[i] receives the
+ * first n <= max_steps with sigma_top(n) == sigma_bottom(n), or max_steps + 1
+ * if they never met.  dev_scratch: shk_coalescence_scratch_bytes(n_pairs)
+ * device bytes owned by the caller.  Synchronous (waits for the result). */
+size_t shk_coalescence_scratch_bytes(int n_pairs);
+int shk_coalescence_times(int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
+                          const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch, size_t bytes,
+                          uint64_t* host_T, void* stream);
+
 /* ------------------------------------------------------------ lattice handle */
 
 typedef struct shk_lattice shk_lattice;

@@ -125,3 +125,50 @@ def critical_J(q):
     """J_c(q) of Eq. J_di_q (the solution of 1 = 2 tanh J tanh q + tanh^2 J)."""
     t = np.tanh(q)
     return np.arctanh(np.sqrt(t * t + 1.0) - t)
+
+
+# ---- square-lattice Ising model and its checkerboard heat bath (Section 3.2)
+
+def square_energy(L: int, J: float) -> np.ndarray:
+    """H_G(s) = -J sum_x s_x (s_{x up} + s_{x right}) for every state code."""
+    S = spin_table(L * L)
+    up, right, _, _ = neighbours(L)
+    return -J * np.sum(S * (S[:, up] + S[:, right]), axis=1)
+
+
+def square_gibbs(L: int, J: float) -> np.ndarray:
+    H = square_energy(L, J)
+    w = np.exp(-(H - H.min()))
+    return w / w.sum()
+
+
+def checkerboard_kernel(L: int, J: float, parity: int, T5=None) -> np.ndarray:
+    """Heat-bath redraw of the sites with (i + j) % 2 == parity given the
+    others, as a dense matrix over state codes (exact probabilities
+    e^{h}/(2 cosh h), h = J * sum of the four neighbours, or the quantised
+    T5[n] / 2^32 with n the number of + neighbours)."""
+    N = L * L
+    S = spin_table(N)
+    up, right, down, left = neighbours(L)
+    j, i = np.divmod(np.arange(N), L)
+    active = ((i + j) % 2) == parity
+    nplus = (S[:, up] > 0).astype(np.int64) + (S[:, down] > 0) + (S[:, left] > 0) + (S[:, right] > 0)
+    if T5 is None:
+        p_up = 0.5 * (1.0 + np.tanh(J * (2.0 * nplus - 4.0)))
+    else:
+        p_up = np.asarray(T5, dtype=np.float64)[nplus] / 2.0 ** 32
+    n_states = 2 ** N
+    K = np.zeros((n_states, n_states))
+    act = np.nonzero(active)[0]
+    for a in range(n_states):
+        base = S[a].copy()
+        for bits in range(2 ** len(act)):
+            prob = 1.0
+            new = base.copy()
+            for k, site in enumerate(act):
+                v = 1 if (bits >> k) & 1 else -1
+                new[site] = v
+                prob *= p_up[a, site] if v > 0 else 1.0 - p_up[a, site]
+            code = int(np.sum((new > 0).astype(np.int64) << np.arange(N)))
+            K[a, code] += prob
+    return K

@@ -43,6 +43,14 @@ def lib() -> ctypes.CDLL:
     so.orc_observables.restype = None
     so.orc_run.argtypes = [_ptr, _ptr, _int, _dbl, _dbl, _u64, _u32, _u64, _u64, _ptr]
     so.orc_run.restype = _int
+    so.orc_diag_correlations.argtypes = [_ptr, _int, _ptr, _int, _ptr]
+    so.orc_diag_correlations.restype = None
+    so.orc_checkerboard_thresholds.argtypes = [_dbl, _ptr]
+    so.orc_checkerboard_thresholds.restype = _int
+    so.orc_checkerboard_halfstep.argtypes = [_ptr, _int, _ptr, _u64, _u32, _u32, _int]
+    so.orc_checkerboard_halfstep.restype = None
+    so.orc_checkerboard_run.argtypes = [_ptr, _int, _dbl, _u64, _u32, _u64, _u64, _ptr]
+    so.orc_checkerboard_run.restype = _int
     so.orc_many_chains.argtypes = [_int, _dbl, _dbl, _u64, _u32, _i64, _ptr, _u64, _ptr, _ptr]
     so.orc_many_chains.restype = _int
     return so
@@ -130,3 +138,36 @@ def many_chains(L: int, q: float, J: float, seed: int, id0: int, M: int,
     if rc != 0:
         raise ValueError("invalid arguments")
     return (cs, ct) if want_tau else cs
+
+
+def diag_correlations(sigma: np.ndarray, L: int, lags) -> np.ndarray:
+    """SW-NE sums then NW-SE sums (see orc_diag_correlations)."""
+    s = np.ascontiguousarray(sigma, dtype=np.int8).reshape(-1)
+    lg = np.ascontiguousarray(lags, dtype=np.int32)
+    out = np.zeros(2 * lg.size, dtype=np.int64)
+    lib().orc_diag_correlations(_p(s), L, _p(lg), int(lg.size), _p(out))
+    return out
+
+
+def checkerboard_thresholds(J: float) -> np.ndarray:
+    out = np.zeros(5, dtype=np.uint32)
+    if lib().orc_checkerboard_thresholds(J, _p(out)) != 0:
+        raise ValueError("J must be finite")
+    return out
+
+
+def checkerboard_halfstep(s: np.ndarray, L: int, T5, seed: int, lattice_id: int, hs: int, parity: int) -> np.ndarray:
+    """In place: redraw the sites with (i + j) % 2 == parity."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    T = np.ascontiguousarray(T5, dtype=np.uint32)
+    lib().orc_checkerboard_halfstep(_p(s), L, _p(T), seed, lattice_id, hs, parity)
+    return s
+
+
+def checkerboard_run(s: np.ndarray, L: int, J: float, seed: int, lattice_id: int, t0: int, n: int):
+    """n full checkerboard steps in place; returns (n, 2) rows of (M, C_nn)."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    obs = np.zeros((max(n, 1), 2), dtype=np.int64)
+    if lib().orc_checkerboard_run(_p(s), L, J, seed, lattice_id, t0, n, _p(obs)) != 0:
+        raise ValueError("invalid checkerboard arguments (L must be even)")
+    return obs[:n]

@@ -272,3 +272,86 @@ int orc_many_chains(int L, double q, double J, uint64_t seed, uint32_t id0, int6
     free(s); free(t);
     return 0;
 }
+
+/* Diagonal spin-spin sums of Section 3.3 (Table 1), translation-averaged:
+ * out[k] = sum_x s_x s_{x+(l,l)} (SW-NE), out[n+k] = sum_x s_x s_{x+(l,-l)}
+ * (NW-SE: the pair (0,l), (l,0)), x = (i, j), l = lags[k]. */
+void orc_diag_correlations(const int8_t* s, int L, const int* lags, int n, int64_t* out) {
+    for (int k = 0; k < n; ++k) {
+        int64_t l = lags[k], a = 0, b = 0;
+        for (int64_t j = 0; j < L; ++j) {
+            for (int64_t i = 0; i < L; ++i) {
+                int64_t x = j * L + i;
+                int64_t y1 = orc_wrap(j + l, L) * L + orc_wrap(i + l, L);
+                int64_t y2 = orc_wrap(j - l, L) * L + orc_wrap(i + l, L);
+                a += (int64_t)s[x] * s[y1];
+                b += (int64_t)s[x] * s[y2];
+            }
+        }
+        out[k] = a;
+        out[n + k] = b;
+    }
+}
+
+/* ------------------------------------------------- checkerboard heat bath */
+
+/* The comparison dynamics of Section 3.2 for the square-lattice Ising model
+ * H_G(s) = -J sum_x s_x (s_{x up} + s_{x right}): the even sites (i + j even)
+ * are redrawn given the odd ones, then the odd sites given the even ones,
+ * each with P(s_x = +1) = e^{h}/(2 cosh h), h = J (sum of the four
+ * neighbours) (heat bath).  Thresholds by the rule of reading R4, indexed by
+ * the number n = 0..4 of + neighbours, h = J (2n - 4).  The uniform of site u
+ * in half-step hs is the block uniform of reading R5 with counter
+ * (hs, u >> 5, lattice_id, 512 + c). */
+int orc_checkerboard_thresholds(double J, uint32_t T[5]) {
+    if (!isfinite(J)) return -1;
+    for (int n = 0; n < 5; ++n) T[n] = orc_threshold_of(J * (double)(2 * n - 4));
+    return 0;
+}
+
+void orc_checkerboard_halfstep(int8_t* s, int L, const uint32_t T[5], uint64_t seed,
+                               uint32_t lattice_id, uint32_t hs, int parity) {
+    uint32_t r[32];
+    int64_t cached_w = -1;
+    for (int64_t j = 0; j < L; ++j) {
+        for (int64_t i = 0; i < L; ++i) {
+            if (((i + j) & 1) != parity) continue;
+            int64_t u = j * L + i;
+            int n = (s[orc_wrap(j + 1, L) * L + i] > 0) + (s[orc_wrap(j - 1, L) * L + i] > 0) +
+                    (s[j * L + orc_wrap(i + 1, L)] > 0) + (s[j * L + orc_wrap(i - 1, L)] > 0);
+            int64_t w = u >> 5;
+            if (w != cached_w) {
+                orc_block_uniforms(seed, hs, (uint32_t)w, lattice_id, 2u, r);
+                cached_w = w;
+            }
+            s[u] = (r[u & 31] < T[n]) ? 1 : -1;
+        }
+    }
+}
+
+/* n full steps t = t0 .. t0+n-1 (even sites with hs = 2t, then odd sites with
+ * hs = 2t + 1), in place; obs (nullable) receives n rows of (M, C_nn) where
+ * C_nn = sum_x s_x (s_{x up} + s_{x right}), so H_G = -J C_nn.  L even. */
+int orc_checkerboard_run(int8_t* s, int L, double J, uint64_t seed, uint32_t lattice_id,
+                         uint64_t t0, uint64_t n, int64_t* obs) {
+    uint32_t T[5];
+    if (L < 2 || (L & 1) || orc_checkerboard_thresholds(J, T) != 0) return -1;
+    if (t0 + n > 0x80000000ull) return -1;
+    for (uint64_t k = 0; k < n; ++k) {
+        uint64_t t = t0 + k;
+        orc_checkerboard_halfstep(s, L, T, seed, lattice_id, (uint32_t)(2 * t), 0);
+        orc_checkerboard_halfstep(s, L, T, seed, lattice_id, (uint32_t)(2 * t + 1), 1);
+        if (obs) {
+            int64_t m = 0, c = 0;
+            for (int64_t j = 0; j < L; ++j)
+                for (int64_t i = 0; i < L; ++i) {
+                    int64_t u = j * L + i;
+                    m += s[u];
+                    c += (int64_t)s[u] * (s[orc_wrap(j + 1, L) * L + i] + s[j * L + orc_wrap(i + 1, L)]);
+                }
+            obs[2 * k] = m;
+            obs[2 * k + 1] = c;
+        }
+    }
+    return 0;
+}

@@ -39,6 +39,9 @@ SIGNATURES = {
     "shk_sweep_variant_name": (_c.c_char_p, [_i, _i]),
     "shk_get_sweep_variant": (_i, [_i]),
     "shk_set_sweep_variant": (_i, [_i, _i]),
+    "shk_diag_correlations": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
+    "shk_coalescence_scratch_bytes": (_sz, [_i]),
+    "shk_coalescence_times": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp, _vp]),
     "shk_init_plane": (_i, [_i, _vp, _i, _i, _u64, _u32, _u32, _vp]),
     "shk_lattice_bytes": (_sz, [_i, _i]),
     "shk_lattice_create": (_i, [_i, _i, _vp, _sz, _vp, _vp]),

@@ -4,6 +4,7 @@
 // lattice handles over caller-owned device memory, dispatch of a run to the
 // one-CTA path (small lattices) or to the grid-wide half-step sweeps, and the
 // observable ring that keeps the last step's sums on the device.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -201,6 +202,63 @@ int shk_get_sweep_variant(int layout) {
 int shk_set_sweep_variant(int layout, int variant) {
     if (!set_sweep_variant(layout, variant))
         return fail(nullptr, SHK_EINVAL, "shk_set_sweep_variant: no variant %d for layout %d", variant, layout);
+    return SHK_OK;
+}
+
+int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags, int64_t* out, void* stream) {
+    Geometry g;
+    if (!make_geometry(L, kBitpack, &g))
+        return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
+    if (plane == nullptr || out == nullptr || lags == nullptr)
+        return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: NULL argument");
+    if (n_lags < 1 || n_lags > 8) return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: n_lags must be 1..8");
+    for (int k = 0; k < n_lags; ++k)
+        if (lags[k] < 0 || lags[k] >= L)
+            return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: lag %d outside 0..L-1", lags[k]);
+    const cudaError_t e = launch_diag_corr(g, plane, lags, n_lags, reinterpret_cast<long long*>(out),
+                                           static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_diag_correlations launch");
+    return SHK_OK;
+}
+
+size_t shk_coalescence_scratch_bytes(int n_pairs) {
+    if (n_pairs <= 0) return 0;
+    return (((size_t)n_pairs * coalesce_pair_bytes() + 255) & ~(size_t)255) + (size_t)n_pairs * 8;
+}
+
+int shk_coalescence_times(int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
+                          const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch, size_t bytes,
+                          uint64_t* host_T, void* stream) {
+    if (n_pairs <= 0 || !L || !q || !J || !seed || !lattice_id || !dev_scratch || !host_T)
+        return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: bad argument");
+    if (bytes < shk_coalescence_scratch_bytes(n_pairs))
+        return fail(nullptr, SHK_ENOMEM, "shk_coalescence_times: %zu bytes given, %zu needed", bytes,
+                    shk_coalescence_scratch_bytes(n_pairs));
+    if (max_steps == 0 || max_steps >= SHK_MAX_STEP)
+        return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: max_steps must be in 1..2^31-1");
+    int max_L = 32;
+    std::vector<unsigned char> host((size_t)n_pairs * coalesce_pair_bytes());
+    for (int i = 0; i < n_pairs; ++i) {
+        if (L[i] < 32 || L[i] > 256 || L[i] % 32 != 0)
+            return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: pair %d has L=%d (need 32..256, L %% 32 == 0)",
+                        i, L[i]);
+        uint32_t T[6];
+        if (host_thresholds(q[i], J[i], T) != SHK_OK)
+            return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: pair %d has non-finite q or J", i);
+        DrawParams P;
+        make_draw_params(seed[i], lattice_id[i], T, 0u, &P);
+        fill_coalesce_pair(host.data() + (size_t)i * coalesce_pair_bytes(), L[i], P);
+        max_L = std::max(max_L, L[i]);
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* dev = static_cast<unsigned char*>(dev_scratch);
+    const size_t off_T = ((size_t)n_pairs * coalesce_pair_bytes() + 255) & ~(size_t)255;
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_coalesce(dev, (uint32_t)n_pairs, max_L, max_steps, reinterpret_cast<unsigned long long*>(dev + off_T), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_T, dev + off_T, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_coalescence_times");
     return SHK_OK;
 }
 

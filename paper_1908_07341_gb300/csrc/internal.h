@@ -50,6 +50,18 @@ const char* sweep_variant_name(int layout, int v);
 int get_sweep_variant(int layout);
 bool set_sweep_variant(int layout, int v);
 
+// Diagonal correlation sums of a bit-packed plane added to out (SW-NE then
+// NW-SE, n_lags each; n_lags <= 8).
+cudaError_t launch_diag_corr(const Geometry& g, const void* plane, const int* lags, int n_lags, long long* out,
+                             cudaStream_t st);
+
+// Coupled top/bottom chains (coalescence times); one CTA per pair.
+size_t coalesce_smem_bytes(int L);
+size_t coalesce_pair_bytes();
+void fill_coalesce_pair(void* dst, int L, const DrawParams& P);
+cudaError_t launch_coalesce(const void* pairs, uint32_t n_pairs, int max_L, uint64_t max_steps,
+                            unsigned long long* T, cudaStream_t st);
+
 // C_nn of a sigma plane added to obs[4].
 cudaError_t launch_cnn(const Geometry& g, const void* sigma, long long* obs, cudaStream_t st);
 

@@ -764,6 +764,164 @@ __global__ void __launch_bounds__(256) k_cnn(const SweepArgs a) {
     block_accumulate<1>(v, d);
 }
 
+// ------------------------------------------------------------ diagonal correlations
+
+constexpr int kMaxLags = 8;
+
+struct CorrArgs {
+    const uint32_t* plane;
+    uint32_t L, Wr, nblocks;
+    FastDiv div_row;
+    int n_lags;
+    uint32_t lag[kMaxLags];
+    long long* out;      // [0, n_lags): SW-NE sums, [n_lags, 2 n_lags): NW-SE sums
+};
+
+// Bits of sites (i + l .. i + l + 31, row) for the block whose first site is
+// i = 32 c, read from a bit-packed row with wrap-around.
+__device__ __forceinline__ uint32_t shifted_row_word(const uint32_t* row, uint32_t c, uint32_t l, uint32_t Wr) {
+    const uint32_t cw = (c + (l >> 5)) % Wr;
+    const uint32_t sh = l & 31u;
+    const uint32_t lo = row[cw];
+    if (sh == 0) return lo;
+    const uint32_t hi = row[cw + 1 == Wr ? 0 : cw + 1];
+    return (lo >> sh) | (hi << (32u - sh));
+}
+
+// sum_x s_x s_{x+(l,l)} and sum_x s_x s_{x+(l,-l)} for every lag (Section
+// 3.3: the SW-NE pair (0,0)-(l,l) and the NW-SE pair (0,l)-(l,0), averaged
+// over translations of the torus).
+__global__ void __launch_bounds__(256) k_diag_corr(const CorrArgs a) {
+    int acc[2 * kMaxLags];
+#pragma unroll
+    for (int k = 0; k < 2 * kMaxLags; ++k) acc[k] = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
+        const uint32_t j = fdiv(w, a.div_row), c = w - j * a.Wr;
+        const uint32_t s = a.plane[w];
+#pragma unroll
+        for (int k = 0; k < kMaxLags; ++k) {
+            if (k < a.n_lags) {
+                const uint32_t l = a.lag[k];
+                const uint32_t jp = j + l >= a.L ? j + l - a.L : j + l;
+                const uint32_t jm = j >= l ? j - l : j + a.L - l;
+                const uint32_t p1 = shifted_row_word(a.plane + (size_t)jp * a.Wr, c, l, a.Wr);
+                const uint32_t p2 = shifted_row_word(a.plane + (size_t)jm * a.Wr, c, l, a.Wr);
+                acc[k] += 32 - 2 * __popc(s ^ p1);
+                acc[kMaxLags + k] += 32 - 2 * __popc(s ^ p2);
+            }
+        }
+    }
+    __shared__ long long red[2 * kMaxLags][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 2 * kMaxLags; ++k) {
+        const int v = warp_sum(acc[k]);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kMaxLags) {
+        const int k = threadIdx.x;
+        const int lk = k < kMaxLags ? k : k - kMaxLags;
+        if (lk < a.n_lags) {
+            long long t = 0;
+            for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[k][i];
+            const int idx = k < kMaxLags ? lk : a.n_lags + lk;
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.out + idx), (unsigned long long)t);
+        }
+    }
+}
+
+// ------------------------------------------------------------ coalescence
+
+struct CoalescePair {
+    uint32_t L, Wr, nblocks;
+    uint32_t pad;
+    DrawParams P;
+};
+
+struct CoalesceArgs {
+    const CoalescePair* pairs;
+    uint32_t n_pairs;
+    unsigned long long max_steps;
+    unsigned long long* T;      // per pair: first n with sigma_top == sigma_bottom, or max_steps + 1
+};
+
+// Bits of block w and of its two field neighbours in a bit-packed shared-
+// memory plane (rows of Wr words, L rows, wrapping).
+template <int HALF>
+__device__ __forceinline__ void smem_fields(const uint32_t* pl, uint32_t w, uint32_t Wr, uint32_t L,
+                                            uint32_t nblocks, uint32_t& S, uint32_t& N1, uint32_t& N2) {
+    const uint32_t row = w / Wr, col = w - row * Wr;
+    words_aligned<HALF>(pl, w, row, col, L, Wr, nblocks, S, N1, N2);
+}
+
+// Section 3.2: two copies of the chain, from all + (top) and all - (bottom),
+// driven by the same random numbers (the same seed, lattice id and steps).
+// The order is preserved, and once the sigma planes agree they agree forever;
+// T is the first step count n with sigma_top(n) == sigma_bottom(n).  One CTA
+// per pair, all four planes in shared memory.
+__global__ void __launch_bounds__(256) k_coalesce(const CoalesceArgs a) {
+    extern __shared__ uint32_t planes[];
+    const uint32_t pi = blockIdx.x;
+    if (pi >= a.n_pairs) return;
+    const CoalescePair& cp = a.pairs[pi];
+    const uint32_t nb = cp.nblocks, Wr = cp.Wr, L = cp.L;
+    const uint32_t nbp = (nb + 31u) & ~31u;
+    uint32_t* st = planes;            // top sigma
+    uint32_t* tt = planes + nbp;      // top tau
+    uint32_t* sb = planes + 2 * nbp;  // bottom sigma
+    uint32_t* tb = planes + 3 * nbp;  // bottom tau
+    for (uint32_t w = threadIdx.x; w < nbp; w += blockDim.x) {
+        st[w] = w < nb ? 0xffffffffu : 0u;
+        sb[w] = 0u;
+        tt[w] = tb[w] = 0u;
+    }
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned long long T = a.max_steps + 1;
+    for (unsigned long long t = 0; t < a.max_steps; ++t) {
+        const uint32_t hs = (uint32_t)(2 * t);
+        for (int half = 0; half < 2; ++half) {
+            for (uint32_t base = warp * 32; base < nbp; base += nwarps * 32) {
+                const uint32_t w = base + lane;
+                const bool in = w < nb;
+                uint32_t S0 = 0, A0 = 0, B0 = 0, S1 = 0, A1 = 0, B1 = 0;
+                if (in) {
+                    if (half == 0) {
+                        smem_fields<0>(st, w, Wr, L, nb, S0, A0, B0);
+                        smem_fields<0>(sb, w, Wr, L, nb, S1, A1, B1);
+                    } else {
+                        smem_fields<1>(tt, w, Wr, L, nb, S0, A0, B0);
+                        smem_fields<1>(tb, w, Wr, L, nb, S1, A1, B1);
+                    }
+                }
+                const uint32_t S[2] = {S0, S1}, A[2] = {A0, A1}, B[2] = {B0, B1}, ww[2] = {w, w};
+                const uint32_t v[2] = {in ? 0xffffffffu : 0u, in ? 0xffffffffu : 0u};
+                uint32_t up[2];
+                draw_blocks<2>(S, A, B, ww, v, hs + (uint32_t)half, cp.P, up);
+                if (in) {
+                    if (half == 0) {
+                        tt[w] = up[0];
+                        tb[w] = up[1];
+                    } else {
+                        st[w] = up[0];
+                        sb[w] = up[1];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        uint32_t diff = 0;
+        for (uint32_t w = threadIdx.x; w < nb; w += blockDim.x) diff |= st[w] ^ sb[w];
+        if (!__syncthreads_or(diff != 0u)) {
+            T = t + 1;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) a.T[pi] = T;
+}
+
 // ------------------------------------------------------------ initial states
 
 struct InitArgs {
@@ -1122,6 +1280,50 @@ cudaError_t launch_init(const Geometry& g, void* plane, int kind, uint64_t init_
         k_init<kInt8><<<grid_for(k_init<kInt8>, block, g.nblocks), block, 0, st>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_diag_corr(const Geometry& g, const void* plane, const int* lags, int n_lags, long long* out,
+                             cudaStream_t st) {
+    CorrArgs a;
+    a.plane = static_cast<const uint32_t*>(plane);
+    a.L = (uint32_t)g.L;
+    a.Wr = g.Wr;
+    a.nblocks = g.nblocks;
+    a.div_row = make_fastdiv(g.Wr);
+    a.n_lags = n_lags;
+    for (int k = 0; k < kMaxLags; ++k) a.lag[k] = k < n_lags ? (uint32_t)lags[k] : 0u;
+    a.out = out;
+    k_diag_corr<<<grid_for(k_diag_corr, 256, g.nblocks), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+size_t coalesce_smem_bytes(int L) { return 4 * (size_t)(((L * L / 32) + 31) & ~31) * 4; }
+
+cudaError_t launch_coalesce(const void* pairs, uint32_t n_pairs, int max_L, uint64_t max_steps,
+                            unsigned long long* T, cudaStream_t st) {
+    CoalesceArgs a;
+    a.pairs = static_cast<const CoalescePair*>(pairs);
+    a.n_pairs = n_pairs;
+    a.max_steps = max_steps;
+    a.T = T;
+    const size_t smem = coalesce_smem_bytes(max_L);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_coalesce, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_coalesce<<<n_pairs, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+size_t coalesce_pair_bytes() { return sizeof(CoalescePair); }
+
+void fill_coalesce_pair(void* dst, int L, const DrawParams& P) {
+    CoalescePair* c = static_cast<CoalescePair*>(dst);
+    c->L = (uint32_t)L;
+    c->Wr = (uint32_t)L / 32;
+    c->nblocks = (uint32_t)((int64_t)L * L / 32);
+    c->pad = 0;
+    c->P = P;
 }
 
 static uint32_t small_block_threads(const Geometry& g) {

@@ -74,6 +74,34 @@ def init_plane(layout, plane: torch.Tensor, L: int, kind="random", init_seed: in
                                int(init_seed), int(lattice_id), int(plane_index), _stream_ptr(stream)))
 
 
+def diag_correlations(plane: torch.Tensor, L: int, lags, stream=None) -> torch.Tensor:
+    """SW-NE and NW-SE spin sums of a bit-packed device plane for each lag
+    (int64 device tensor of 2 * len(lags): SW-NE first)."""
+    lg = np.ascontiguousarray(lags, dtype=np.int32)
+    out = torch.zeros(2 * lg.size, dtype=torch.int64, device=plane.device)
+    check(lib().shk_diag_correlations(plane.data_ptr(), int(L), lg.ctypes.data, int(lg.size), out.data_ptr(),
+                                      _stream_ptr(stream)))
+    return out
+
+
+def coalescence_times(L, q, J, seed, lattice_id, max_steps: int, device="cuda", stream=None) -> np.ndarray:
+    """Coalescence time of the all + and all - chains of every pair (see
+    shk_coalescence_times); max_steps + 1 where they did not meet."""
+    Ls = np.ascontiguousarray(L, dtype=np.int32)
+    n = Ls.size
+    qs = np.ascontiguousarray(np.broadcast_to(q, (n,)), dtype=np.float64)
+    Js = np.ascontiguousarray(np.broadcast_to(J, (n,)), dtype=np.float64)
+    ss = np.ascontiguousarray(np.broadcast_to(seed, (n,)), dtype=np.uint64)
+    ids = np.ascontiguousarray(np.broadcast_to(lattice_id, (n,)), dtype=np.uint32)
+    nbytes = int(lib().shk_coalescence_scratch_bytes(n))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    out = np.zeros(n, dtype=np.uint64)
+    check(lib().shk_coalescence_times(n, Ls.ctypes.data, qs.ctypes.data, Js.ctypes.data, ss.ctypes.data,
+                                      ids.ctypes.data, int(max_steps), scratch.data_ptr(), nbytes,
+                                      out.ctypes.data, _stream_ptr(stream)))
+    return out
+
+
 def unpack_bits(words: np.ndarray, L: int) -> np.ndarray:
     """Host view of a bit-packed plane as int8 +/-1 of shape (L, L)."""
     w = np.ascontiguousarray(words).view(np.uint32)[: L * L // 32]

@@ -1,0 +1,58 @@
+"""GPU parity of the Section 3 kernels: diagonal correlation sums and
+coalescence times, against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1908_07341_gb300 as shk
+from paper_1908_07341_gb300.lattice import coalescence_times, diag_correlations
+from tests.gpu_util import to_device_plane
+from tests.inputs import random_spins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1908_07341_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+@pytest.mark.parametrize("L", [32, 64, 96, 1024])
+def test_diag_correlations_match_oracle(orc, L):
+    lags = [0, 1, 2, 4, 8, 16, 31, L - 1] if L > 32 else [0, 1, 2, 4, 8, 16, 31]
+    s = random_spins(L, seed=L + 3, p_up=0.6)
+    got = diag_correlations(to_device_plane(s, L, "bitpack"), L, lags).cpu().numpy()
+    assert np.array_equal(got, orc.diag_correlations(s, L, lags))
+
+
+def _oracle_T(orc, L, q, J, seed, lat_id, max_steps):
+    top_s, top_t = np.ones(L * L, np.int8), np.ones(L * L, np.int8)
+    bot_s, bot_t = -np.ones(L * L, np.int8), -np.ones(L * L, np.int8)
+    for t in range(max_steps):
+        orc.run(top_s, top_t, L, q, J, seed, lat_id, t, 1, want_obs=False)
+        orc.run(bot_s, bot_t, L, q, J, seed, lat_id, t, 1, want_obs=False)
+        if np.array_equal(top_s, bot_s):
+            return t + 1
+    return max_steps + 1
+
+
+def test_coalescence_times_match_oracle(orc):
+    """T = min{n : sigma_top(n) = sigma_bottom(n)} of Section 3.2 for coupled
+    chains from all + and all -, computed step by step by the oracle."""
+    pairs = [(32, 0.5, 0.3, 7, 0), (32, 1.0, 0.4, 7, 1), (64, 0.6585, 0.55, 9, 2), (32, 3.0, 0.3, 1, 3),
+             (32, 0.2, 0.9, 2, 4), (96, 0.8, 0.35, 5, 5)]
+    max_steps = 1500
+    L, q, J, seed, ids = (np.array(x) for x in zip(*pairs))
+    got = coalescence_times(L, q, J, seed.astype(np.uint64), ids.astype(np.uint32), max_steps)
+    for k, (l_, q_, j_, s_, i_) in enumerate(pairs):
+        assert int(got[k]) == _oracle_T(orc, l_, q_, j_, s_, i_, max_steps), pairs[k]
+    assert np.any(got <= max_steps)
+
+
+def test_coalescence_not_reached_is_reported():
+    # deep in the ordered phase on a 64x64 torus the chains do not meet quickly
+    got = coalescence_times([64], [2.0], [1.5], [3], [0], 20)
+    assert int(got[0]) == 21

@@ -335,6 +335,9 @@ def test_quantised_stationary_law_is_flip_symmetric(orc):
 
 
 def _chi2_pvalue(counts, probs, min_expected=5.0):
+    impossible = probs == 0
+    assert counts[impossible].sum() == 0, "an outcome of probability zero occurred"
+    counts, probs = counts[~impossible], probs[~impossible]
     exp_ = probs * counts.sum()
     order = np.argsort(exp_)
     small = exp_[order] < min_expected
@@ -510,3 +513,124 @@ def test_critical_curve_printed_values():
     for q in (0.1, 0.5, 1.0, 2.5):
         J = exact.critical_J(q)
         assert abs(2 * np.tanh(J) * np.tanh(q) + np.tanh(J) ** 2 - 1) < 1e-12
+
+
+# ------------------------------------------------- diagonal correlations
+
+def test_diagonal_correlation_sums(orc):
+    """Section 3.3's SW-NE pair (0,0)-(l,l) and NW-SE pair (0,l)-(l,0),
+    averaged over translations: exact values for patterns with known answers
+    and, for random planes, agreement with an independent numpy computation by
+    array rolls."""
+    L = 12
+    i, j = np.meshgrid(np.arange(L), np.arange(L))          # i: column, j: row
+    lags = [0, 1, 2, 3, 5, 11]
+    N = L * L
+    ones = np.ones(N, np.int8)
+    assert np.all(orc.diag_correlations(ones, L, lags) == N)
+    board = np.where((i + j) % 2 == 0, 1, -1).astype(np.int8).ravel()
+    assert np.all(orc.diag_correlations(board, L, lags) == N)
+    cols = np.where(i % 2 == 0, 1, -1).astype(np.int8).ravel()    # depends on the column only
+    got = orc.diag_correlations(cols, L, lags)
+    want = np.array([N * (-1) ** l for l in lags] * 2)
+    assert np.array_equal(got, want)
+    rows_ = np.where(j % 3 == 0, 1, -1).astype(np.int8)       # depends on the row only
+    got = orc.diag_correlations(rows_.ravel(), L, lags)
+    for k, l in enumerate(lags):
+        assert got[k] == np.sum(rows_ * np.roll(rows_, -l, axis=0))
+        assert got[len(lags) + k] == np.sum(rows_ * np.roll(rows_, l, axis=0))
+    rng = np.random.default_rng(1)
+    for L2 in (7, 16):
+        s = rng.choice(np.array([-1, 1], np.int8), size=(L2, L2))
+        got = orc.diag_correlations(s.ravel(), L2, [1, 2, 4])
+        S = s.astype(np.int64)
+        for k, l in enumerate([1, 2, 4]):
+            swne = np.roll(np.roll(S, -l, axis=0), -l, axis=1)   # s at (i+l, j+l)
+            nwse = np.roll(np.roll(S, l, axis=0), -l, axis=1)    # s at (i+l, j-l)
+            assert got[k] == np.sum(S * swne)
+            assert got[3 + k] == np.sum(S * nwse)
+
+
+# ----------------------------------------------- checkerboard heat bath (Section 3.2)
+
+@pytest.mark.parametrize("J", [0.2, 0.4406867, 0.9, -0.5, 0.0])
+def test_checkerboard_thresholds_against_arbitrary_precision(orc, J):
+    """P(+1) = e^{h}/(2 cosh h), h = J (2n - 4) for n = 0..4 + neighbours."""
+    T = orc.checkerboard_thresholds(J)
+    mpmath.mp.dps = 60
+    for n in range(5):
+        h = mpmath.mpf(J) * (2 * n - 4)
+        assert abs(int(T[n]) - mpmath.e ** h / (2 * mpmath.cosh(h)) * mpmath.mpf(2) ** 32) <= 1
+        if h != 0:
+            assert int(T[n]) + int(T[4 - n]) == 2 ** 32
+
+
+@pytest.mark.parametrize("J", [0.3, 0.7])
+def test_checkerboard_kernels_preserve_square_gibbs(J):
+    """Theorem 2.2 of the cited work: each parity's heat-bath redraw leaves the
+    square-lattice Gibbs measure invariant (2x2 torus, exact enumeration)."""
+    pi = exact.square_gibbs(2, J)
+    for parity in (0, 1):
+        K = exact.checkerboard_kernel(2, J, parity)
+        assert np.allclose(K.sum(axis=1), 1.0, atol=1e-13)
+        assert np.max(np.abs(pi @ K - pi)) < 1e-14
+
+
+def test_checkerboard_half_step_law_2x2(orc):
+    """One oracle half-step from a fixed state against the row of the
+    enumerated (quantised) kernel, for both parities (chi-square)."""
+    L, J, M = 2, 0.5, 40000
+    T = orc.checkerboard_thresholds(J)
+    s0 = np.array([1, -1, -1, -1], dtype=np.int8)
+    code0 = 1
+    for parity in (0, 1):
+        K = exact.checkerboard_kernel(L, J, parity, T)
+        counts = np.zeros(16, dtype=np.int64)
+        for lat in range(M):
+            s = s0.copy()
+            orc.checkerboard_halfstep(s, L, T, 11, lat, parity, parity)
+            counts[int(np.sum((s > 0).astype(np.int64) << np.arange(4)))] += 1
+        assert _chi2_pvalue(counts, K[code0]) > 1e-4
+
+
+def test_checkerboard_preserves_gibbs_4x4(orc):
+    """States drawn from the exact 4x4 square-lattice Gibbs measure stay
+    Gibbs-distributed under the oracle's checkerboard steps: chi-square on the
+    joint histogram of (magnetisation, energy)."""
+    L, J, M, n = 4, 0.4, 30000, 3
+    S = exact.spin_table(16)
+    pi = exact.square_gibbs(L, J)
+    Mag = S.sum(axis=1)
+    up, right, _, _ = exact.neighbours(L)
+    C = np.sum(S * (S[:, up] + S[:, right]), axis=1)
+    key = (Mag + 16) * 100 + (C + 40)
+    keys, inv = np.unique(key, return_inverse=True)
+    probs = np.bincount(inv, weights=pi, minlength=keys.size)
+    rng = np.random.default_rng(44)
+    codes = rng.choice(2 ** 16, size=M, p=pi)
+    counts = np.zeros(keys.size, dtype=np.int64)
+    for k, code in enumerate(codes):
+        s = np.where((int(code) >> np.arange(16)) & 1, 1, -1).astype(np.int8)
+        obs = orc.checkerboard_run(s, L, J, 5, k, 0, n)
+        kk = (obs[-1, 0] + 16) * 100 + (obs[-1, 1] + 40)
+        counts[np.searchsorted(keys, kk)] += 1
+    assert _chi2_pvalue(counts, probs) > 1e-4
+
+
+def test_checkerboard_updates_one_parity_and_follows_strong_coupling(orc):
+    """A half-step changes only the sites of its parity; with J = 20 a site
+    with 3 or 4 + neighbours becomes +, with 0 or 1 becomes -."""
+    L = 8
+    T = orc.checkerboard_thresholds(20.0)
+    rng = np.random.default_rng(3)
+    s = rng.choice(np.array([-1, 1], np.int8), size=L * L)
+    for parity in (0, 1):
+        before = s.copy()
+        orc.checkerboard_halfstep(s, L, T, 1, 0, 4 + parity, parity)
+        j, i = np.divmod(np.arange(L * L), L)
+        other = ((i + j) % 2) != parity
+        assert np.array_equal(s[other], before[other])
+        up, right, down, left = exact.neighbours(L)
+        n = (before[up] > 0).astype(int) + (before[down] > 0) + (before[left] > 0) + (before[right] > 0)
+        mine = ~other
+        assert np.all(s[mine & (n >= 3)] == 1) and np.all(s[mine & (n <= 1)] == -1)
