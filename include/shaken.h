@@ -184,6 +184,21 @@ int shk_coalescence_times(int n_pairs, const int* L, const double* q, const doub
                           const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch, size_t bytes,
                           uint64_t* host_T, void* stream);
 
+/* The comparison dynamics of Section 3.2 for the square-lattice Ising model
+ * H_G(s) = -J sum_x s_x (s_{x up} + s_{x right}) (the paper's parallel heat
+ * bath on odd and even sites, whose stationary law is the Gibbs measure):
+ * step t redraws the sites with i + j even (half-step index 2t), then those
+ * with i + j odd (2t + 1), each +1 with probability e^h / (2 cosh h),
+ * h = J (2n - 4), n the number of + among its four neighbours.  Thresholds
+ * T[n] by the rule of shk_thresholds; the uniform of site u in half-step hs is
+ * the block construction of this header with counter (hs, u >> 5, lattice_id,
+ * 512 + c).  plane: device bit-packed sigma (L % 32 == 0), updated in place;
+ * dev_obs (nullable): n_steps rows of (M, C_nn) int64, H_G = -J C_nn.
+ * Asynchronous. */
+int shk_checkerboard_thresholds(double J, uint32_t out[5]);
+int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
+                         uint64_t n_steps, int64_t* dev_obs, void* stream);
+
 /* ------------------------------------------------------------ lattice handle */
 
 typedef struct shk_lattice shk_lattice;

@@ -42,6 +42,8 @@ SIGNATURES = {
     "shk_diag_correlations": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "shk_coalescence_scratch_bytes": (_sz, [_i]),
     "shk_coalescence_times": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp, _vp]),
+    "shk_checkerboard_thresholds": (_i, [_d, _vp]),
+    "shk_checkerboard_run": (_i, [_vp, _i, _d, _u64, _u32, _u64, _u64, _vp, _vp]),
     "shk_init_plane": (_i, [_i, _vp, _i, _i, _u64, _u32, _u32, _vp]),
     "shk_lattice_bytes": (_sz, [_i, _i]),
     "shk_lattice_create": (_i, [_i, _i, _vp, _sz, _vp, _vp]),

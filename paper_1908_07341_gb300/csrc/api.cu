@@ -221,6 +221,40 @@ int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags,
     return SHK_OK;
 }
 
+int shk_checkerboard_thresholds(double J, uint32_t out[5]) {
+    if (!std::isfinite(J) || out == nullptr)
+        return fail(nullptr, SHK_EINVAL, "shk_checkerboard_thresholds: J must be finite and out non-NULL");
+    for (int n = 0; n < 5; ++n) out[n] = threshold_of(J * (double)(2 * n - 4));
+    return SHK_OK;
+}
+
+int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
+                         uint64_t n_steps, int64_t* dev_obs, void* stream) {
+    Geometry g;
+    if (!make_geometry(L, kBitpack, &g))
+        return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
+    if (plane == nullptr) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: plane is NULL");
+    if (t0 + n_steps > SHK_MAX_STEP) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: step index would exceed 2^31");
+    uint32_t T5[5];
+    if (shk_checkerboard_thresholds(J, T5) != SHK_OK) return SHK_EINVAL;
+    const uint32_t T6[6] = {0u - T5[4], 0u - T5[3], 0u - T5[2], T5[2], T5[3], T5[4]};
+    DrawParams P;
+    make_draw_params(seed, lattice_id, T6, 2u, &P);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (dev_obs) {
+        const cudaError_t e = cudaMemsetAsync(dev_obs, 0, (size_t)n_steps * 2 * sizeof(int64_t), st);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_checkerboard_run memset");
+    }
+    for (uint64_t k = 0; k < n_steps; ++k) {
+        const uint64_t t = t0 + k;
+        long long* row = dev_obs ? reinterpret_cast<long long*>(dev_obs) + 2 * k : nullptr;
+        cudaError_t e = launch_checkerboard(g, plane, P, (uint32_t)(2 * t), 0, nullptr, st);
+        if (e == cudaSuccess) e = launch_checkerboard(g, plane, P, (uint32_t)(2 * t + 1), 1, row, st);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_checkerboard_run launch");
+    }
+    return SHK_OK;
+}
+
 size_t shk_coalescence_scratch_bytes(int n_pairs) {
     if (n_pairs <= 0) return 0;
     return (((size_t)n_pairs * coalesce_pair_bytes() + 255) & ~(size_t)255) + (size_t)n_pairs * 8;

@@ -205,6 +205,21 @@ __device__ __forceinline__ uint32_t draw_rest(const BlockClass& k, uint32_t w, u
     return up | (und & k.F);
 }
 
+// One block with precomputed class masks (lazy loop to the end; all lanes of
+// the warp call it together).
+template <class PP>
+__device__ __forceinline__ uint32_t draw_block_class(const BlockClass& k, uint32_t w, uint32_t valid,
+                                                     uint32_t hs, const PP& P) {
+    uint32_t und = valid, up = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint4 R = philox_call(w, hs, c, P);
+        apply_planes(R, c, k, und, up, P);
+        if (c < 7 && !__any_sync(0xffffffffu, und != 0u)) break;
+    }
+    return up | (und & k.F);
+}
+
 // One block (the common case).
 template <class PP>
 __device__ __forceinline__ uint32_t draw_block(uint32_t S, uint32_t A, uint32_t B, uint32_t w,

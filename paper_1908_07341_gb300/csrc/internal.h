@@ -62,6 +62,12 @@ void fill_coalesce_pair(void* dst, int L, const DrawParams& P);
 cudaError_t launch_coalesce(const void* pairs, uint32_t n_pairs, int max_L, uint64_t max_steps,
                             unsigned long long* T, cudaStream_t st);
 
+// Checkerboard heat-bath half-step in place on a bit-packed plane; after the
+// odd half (parity 1) the magnetisation and C_nn are added to obs[0..1]
+// (obs nullable).
+cudaError_t launch_checkerboard(const Geometry& g, void* plane, const DrawParams& P, uint32_t hs, int parity,
+                                long long* obs, cudaStream_t st);
+
 // C_nn of a sigma plane added to obs[4].
 cudaError_t launch_cnn(const Geometry& g, const void* sigma, long long* obs, cudaStream_t st);
 

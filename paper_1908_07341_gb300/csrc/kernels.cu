@@ -922,6 +922,66 @@ __global__ void __launch_bounds__(256) k_coalesce(const CoalesceArgs a) {
     if (threadIdx.x == 0) a.T[pi] = T;
 }
 
+// ------------------------------------------------------------ checkerboard heat bath
+
+// The square-lattice comparison dynamics of Section 3.2: the sites with
+// (i + j) % 2 == PARITY are redrawn in place, P(+1) = e^h / (2 cosh h) with
+// h = J (2n - 4), n the number of + among the four neighbours (all of the
+// other parity, so unchanged by this launch).  With the complement rule the
+// five thresholds fold onto the three-class draw: sites with n < 2 compare
+// their complemented uniform, and the class is n' = max(n, 4 - n) in {2, 3, 4}
+// with thresholds (T[2], T[3], T[4]).
+template <int PARITY>
+__global__ void __launch_bounds__(256) k_checkerboard(const SweepArgs a) {
+    uint32_t* pl = static_cast<uint32_t*>(a.dst);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
+        const uint32_t w = base + lane;
+        const uint32_t row = fdiv(w, a.div_row);
+        const uint32_t col = w - row * a.Wr;
+        const uint32_t S = pl[w];
+        const uint32_t U = pl[row + 1 < a.L ? w + a.Wr : w + a.Wr - a.nblocks];
+        const uint32_t D = pl[row > 0 ? w - a.Wr : w + a.nblocks - a.Wr];
+        const uint32_t prev = pl[col > 0 ? w - 1 : w + a.Wr - 1];
+        const uint32_t next = pl[col + 1 < a.Wr ? w + 1 : w + 1 - a.Wr];
+        const uint32_t Lf = (S << 1) | (prev >> 31);
+        const uint32_t Rt = (S >> 1) | (next << 31);
+        // n = U + D + Lf + Rt per site, as bits b0 + 2 b1 + 4 b2
+        const uint32_t ab_s = U ^ D, ab_c = U & D, cd_s = Lf ^ Rt, cd_c = Lf & Rt;
+        const uint32_t b0 = ab_s ^ cd_s, c0 = ab_s & cd_s;
+        const uint32_t b1 = ab_c ^ cd_c ^ c0;
+        const uint32_t b2 = (ab_c & cd_c) | ((ab_c ^ cd_c) & c0);
+        const uint32_t extreme = b2 | ~(b0 | b1 | b2);       // n == 4 or n == 0
+        BlockClass k;
+        k.F = ~(b1 | b2);                                   // n < 2
+        k.C2 = extreme;
+        k.Cg = b0 | extreme;                                // n odd or extreme
+        const uint32_t pm = ((row & 1u) == (uint32_t)PARITY) ? 0x55555555u : 0xAAAAAAAAu;
+        const uint32_t up = draw_block_class(k, w, pm, a.hs, a.P);
+        pl[w] = (S & ~pm) | (up & pm);
+    }
+}
+
+// Magnetisation and C_nn = sum_x s_x (s_{x down} + s_{x left}) (equal by
+// translation to the up/right form) of a bit-packed plane, added to out[0..1].
+__global__ void __launch_bounds__(256) k_sq_obs(const SweepArgs a) {
+    int m = 0, c = 0;
+    const uint32_t* pl = static_cast<const uint32_t*>(a.src);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
+        const uint32_t row = fdiv(w, a.div_row);
+        uint32_t S, N1, N2;
+        words_aligned<0>(pl, w, row, w - row * a.Wr, a.L, a.Wr, a.nblocks, S, N1, N2);
+        m += 2 * __popc(S) - 32;
+        c += 64 - 2 * (__popc(S ^ N1) + __popc(S ^ N2));
+    }
+    const int v[2] = {m, c};
+    long long* const d[2] = {a.obs_cur, a.obs_cur ? a.obs_cur + 1 : nullptr};
+    block_accumulate<2>(v, d);
+}
+
 // ------------------------------------------------------------ initial states
 
 struct InitArgs {
@@ -1324,6 +1384,21 @@ void fill_coalesce_pair(void* dst, int L, const DrawParams& P) {
     c->nblocks = (uint32_t)((int64_t)L * L / 32);
     c->pad = 0;
     c->P = P;
+}
+
+cudaError_t launch_checkerboard(const Geometry& g, void* plane, const DrawParams& P, uint32_t hs, int parity,
+                                long long* obs, cudaStream_t st) {
+    SweepArgs a = sweep_args(g, plane, plane, P, hs, obs, nullptr, nullptr);
+    const int block = 256;
+    if (parity == 0) {
+        k_checkerboard<0><<<grid_for(k_checkerboard<0>, block, g.nblocks), block, 0, st>>>(a);
+    } else {
+        k_checkerboard<1><<<grid_for(k_checkerboard<1>, block, g.nblocks), block, 0, st>>>(a);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && obs != nullptr && parity == 1)
+        k_sq_obs<<<grid_for(k_sq_obs, block, g.nblocks), block, 0, st>>>(a);
+    return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 static uint32_t small_block_threads(const Geometry& g) {

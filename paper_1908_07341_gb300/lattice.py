@@ -102,6 +102,23 @@ def coalescence_times(L, q, J, seed, lattice_id, max_steps: int, device="cuda", 
     return out
 
 
+def checkerboard_thresholds(J: float) -> np.ndarray:
+    out = np.zeros(5, dtype=np.uint32)
+    check(lib().shk_checkerboard_thresholds(float(J), out.ctypes.data))
+    return out
+
+
+def checkerboard_run(plane: torch.Tensor, L: int, J: float, seed: int, lattice_id: int, t0: int, n_steps: int,
+                     obs: bool = True, stream=None):
+    """n_steps checkerboard heat-bath steps in place on a bit-packed device
+    plane; returns the (n_steps, 2) int64 device rows of (M, C_nn) if obs."""
+    out = torch.empty((int(n_steps), 2), dtype=torch.int64, device=plane.device) if obs else None
+    check(lib().shk_checkerboard_run(plane.data_ptr(), int(L), float(J), int(seed) & (2 ** 64 - 1),
+                                     int(lattice_id), int(t0), int(n_steps),
+                                     out.data_ptr() if out is not None else None, _stream_ptr(stream)))
+    return out
+
+
 def unpack_bits(words: np.ndarray, L: int) -> np.ndarray:
     """Host view of a bit-packed plane as int8 +/-1 of shape (L, L)."""
     w = np.ascontiguousarray(words).view(np.uint32)[: L * L // 32]

@@ -56,3 +56,38 @@ def test_coalescence_not_reached_is_reported():
     # deep in the ordered phase on a 64x64 torus the chains do not meet quickly
     got = coalescence_times([64], [2.0], [1.5], [3], [0], 20)
     assert int(got[0]) == 21
+
+
+# ---- checkerboard heat bath of the square-lattice Ising model (Section 3.2)
+
+from paper_1908_07341_gb300.lattice import checkerboard_run  # noqa: E402
+from tests.gpu_util import from_device_plane  # noqa: E402
+
+
+@pytest.mark.parametrize("L,J,n", [(32, 0.44, 3), (64, 0.3, 40), (96, -0.5, 7), (64, 0.0, 5), (32, 9.0, 4),
+                                   (1024, 0.4406868, 3)])
+def test_checkerboard_run_matches_oracle(orc, L, J, n):
+    s = random_spins(L, seed=L + 11, p_up=0.55)
+    plane = to_device_plane(s, L, "bitpack")
+    got_obs = checkerboard_run(plane, L, J, seed=13, lattice_id=2, t0=5, n_steps=n).cpu().numpy()
+    ref = s.copy()
+    ref_obs = orc.checkerboard_run(ref, L, J, 13, 2, 5, n)
+    assert np.array_equal(from_device_plane(plane, L, "bitpack"), ref)
+    assert np.array_equal(got_obs, ref_obs)
+
+
+def test_checkerboard_resume_and_lattice_ids(orc):
+    L = 64
+    s = random_spins(L, seed=5, p_up=0.5)
+    a, b = to_device_plane(s, L, "bitpack"), to_device_plane(s, L, "bitpack")
+    checkerboard_run(a, L, 0.5, 21, 0, 0, 12, obs=False)
+    checkerboard_run(b, L, 0.5, 21, 0, 0, 5, obs=False)
+    checkerboard_run(b, L, 0.5, 21, 0, 5, 7, obs=False)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    c = to_device_plane(s, L, "bitpack")
+    checkerboard_run(c, L, 0.5, 21, 1, 0, 12, obs=False)
+    assert not torch.equal(a, c)
+    ref = s.copy()
+    orc.checkerboard_run(ref, L, 0.5, 21, 1, 0, 12)
+    assert np.array_equal(from_device_plane(c, L, "bitpack"), ref)

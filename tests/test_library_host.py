@@ -125,3 +125,15 @@ def test_batch_arguments_are_checked_without_a_gpu(so):
     assert so.shk_batch_create(2, bad.ctypes.data, q.ctypes.data, J.ctypes.data, seed.ctypes.data,
                                ids.ctypes.data, 256, 1 << 30, None, ctypes.byref(h)) == _lib.EINVAL
     assert b"L=33" in so.shk_last_error(None)
+
+
+def test_checkerboard_argument_checks_without_gpu():
+    so = _lib.lib()
+    dummy = ctypes.c_void_p(16)
+    assert so.shk_checkerboard_run(dummy, 48, 0.4, 1, 0, 0, 1, None, None) == _lib.EINVAL
+    assert so.shk_checkerboard_run(None, 64, 0.4, 1, 0, 0, 1, None, None) == _lib.EINVAL
+    assert so.shk_checkerboard_run(dummy, 64, 0.4, 1, 0, 2 ** 31, 1, None, None) == _lib.EINVAL
+    assert so.shk_checkerboard_run(dummy, 64, float("nan"), 1, 0, 0, 1, None, None) == _lib.EINVAL
+    out = (ctypes.c_uint32 * 5)()
+    assert so.shk_checkerboard_thresholds(float("inf"), out) == _lib.EINVAL
+    assert so.shk_checkerboard_thresholds(0.0, out) == _lib.OK and list(out) == [2 ** 31] * 5
