@@ -51,6 +51,10 @@ def lib() -> ctypes.CDLL:
     so.orc_checkerboard_halfstep.restype = None
     so.orc_checkerboard_run.argtypes = [_ptr, _int, _dbl, _u64, _u32, _u64, _u64, _ptr]
     so.orc_checkerboard_run.restype = _int
+    so.orc_cftp.argtypes = [_int, _int, _dbl, _dbl, _u64, _u32, _int, _ptr]
+    so.orc_cftp.restype = _int
+    so.orc_cftp_many.argtypes = [_int, _int, _dbl, _dbl, _u64, _u32, _i64, _int, _ptr, _ptr]
+    so.orc_cftp_many.restype = _int
     so.orc_many_chains.argtypes = [_int, _dbl, _dbl, _u64, _u32, _i64, _ptr, _u64, _ptr, _ptr]
     so.orc_many_chains.restype = _int
     return so
@@ -171,3 +175,25 @@ def checkerboard_run(s: np.ndarray, L: int, J: float, seed: int, lattice_id: int
     if lib().orc_checkerboard_run(_p(s), L, J, seed, lattice_id, t0, n, _p(obs)) != 0:
         raise ValueError("invalid checkerboard arguments (L must be even)")
     return obs[:n]
+
+
+SHAKEN, CHECKERBOARD = 0, 1
+
+
+def cftp(dyn: int, L: int, q: float, J: float, seed: int, lattice_id: int, k_max: int = 20):
+    """One coupling-from-the-past sample (see orc_cftp): (k, state) with
+    state None when no attempt up to k_max coalesced."""
+    s = np.zeros(L * L, dtype=np.int8)
+    k = lib().orc_cftp(dyn, L, q, J, seed, lattice_id, k_max, _p(s))
+    if k == -2:
+        raise ValueError("invalid cftp arguments")
+    return k, (s if k >= 0 else None)
+
+
+def cftp_many(dyn: int, L: int, q: float, J: float, seed: int, id0: int, M: int, k_max: int = 20):
+    """M samples of a torus with L*L <= 64 as state codes, and their k."""
+    codes = np.zeros(M, dtype=np.uint64)
+    ks = np.zeros(M, dtype=np.int32)
+    if lib().orc_cftp_many(dyn, L, q, J, seed, id0, M, k_max, _p(codes), _p(ks)) != 0:
+        raise ValueError("invalid cftp arguments")
+    return codes, ks

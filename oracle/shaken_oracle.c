@@ -355,3 +355,83 @@ int orc_checkerboard_run(int8_t* s, int L, double J, uint64_t seed, uint32_t lat
     }
     return 0;
 }
+
+/* ---- coupling from the past (Propp-Wilson, Section 3.2) -------------------
+ *
+ * Both dynamics are monotone for J, q >= 0 (the order sigma >= eta of the
+ * paper's footnote is kept by every step driven by the same uniforms), so it
+ * is enough to follow the chains started from all + and all -.  Time runs
+ * from -2^k to 0.  The randomness of the step from time -s to -s + 1 (s >= 1)
+ * must not depend on k: it is that of forward step index s - 1 (half-steps
+ * 2(s-1) and 2(s-1) + 1).  Attempt k = 0, 1, 2, ... runs both chains from
+ * time -2^k to 0; the first attempt after which they agree returns their
+ * common state at time 0, a draw from the stationary law.  For the shaken
+ * dynamics the state compared and returned is sigma (tau is overwritten by
+ * the first half-step and carries no state).
+ * dyn 0 = shaken (q, J), dyn 1 = checkerboard heat bath (J; L even).
+ * Returns the k of the successful attempt, or -1 when none up to k_max
+ * coalesced (sample then holds nothing), -2 on bad arguments. */
+int orc_cftp(int dyn, int L, double q, double J, uint64_t seed, uint32_t lattice_id, int k_max,
+             int8_t* sample) {
+    if (L < 2 || k_max < 0 || k_max > 30 || (dyn != 0 && dyn != 1)) return -2;
+    if (dyn == 1 && (L & 1)) return -2;
+    uint32_t T6[6], T5[5];
+    if (dyn == 0 && orc_thresholds(q, J, T6) != 0) return -2;
+    if (dyn == 1 && orc_checkerboard_thresholds(J, T5) != 0) return -2;
+    const int64_t N = (int64_t)L * L;
+    int8_t* top = (int8_t*)malloc((size_t)N);
+    int8_t* bot = (int8_t*)malloc((size_t)N);
+    int8_t* ttop = (int8_t*)malloc((size_t)N);
+    int8_t* tbot = (int8_t*)malloc((size_t)N);
+    int result = -1;
+    for (int k = 0; k <= k_max && result < 0; ++k) {
+        for (int64_t u = 0; u < N; ++u) {
+            top[u] = 1;
+            bot[u] = -1;
+            ttop[u] = tbot[u] = 1;
+        }
+        for (int64_t s = (int64_t)1 << k; s >= 1; --s) {
+            const uint64_t t = (uint64_t)(s - 1);
+            if (dyn == 0) {
+                orc_run(top, ttop, L, q, J, seed, lattice_id, t, 1, NULL);
+                orc_run(bot, tbot, L, q, J, seed, lattice_id, t, 1, NULL);
+            } else {
+                orc_checkerboard_run(top, L, J, seed, lattice_id, t, 1, NULL);
+                orc_checkerboard_run(bot, L, J, seed, lattice_id, t, 1, NULL);
+            }
+        }
+        if (memcmp(top, bot, (size_t)N) == 0) {
+            memcpy(sample, top, (size_t)N);
+            result = k;
+        }
+    }
+    free(top);
+    free(bot);
+    free(ttop);
+    free(tbot);
+    return result;
+}
+
+/* M independent perfect samples (lattice ids id0 .. id0 + M - 1) as state
+ * codes (bit u set iff the spin at u is +1; N <= 64) and their k. */
+int orc_cftp_many(int dyn, int L, double q, double J, uint64_t seed, uint32_t id0, int64_t M, int k_max,
+                  uint64_t* codes, int32_t* ks) {
+    const int64_t N = (int64_t)L * L;
+    if (N > 64 || M < 0) return -2;
+    int8_t* s = (int8_t*)malloc((size_t)N);
+    for (int64_t m = 0; m < M; ++m) {
+        const int k = orc_cftp(dyn, L, q, J, seed, id0 + (uint32_t)m, k_max, s);
+        if (k == -2) {
+            free(s);
+            return -2;
+        }
+        ks[m] = k;
+        uint64_t c = 0;
+        if (k >= 0)
+            for (int64_t u = 0; u < N; ++u)
+                if (s[u] > 0) c |= (uint64_t)1 << u;
+        codes[m] = c;
+    }
+    free(s);
+    return 0;
+}

@@ -634,3 +634,71 @@ def test_checkerboard_updates_one_parity_and_follows_strong_coupling(orc):
         n = (before[up] > 0).astype(int) + (before[down] > 0) + (before[left] > 0) + (before[right] > 0)
         mine = ~other
         assert np.all(s[mine & (n >= 3)] == 1) and np.all(s[mine & (n <= 1)] == -1)
+
+
+# ---- coupling from the past (Propp-Wilson, Section 3.2)
+
+def _quantised_checkerboard_step(L, J, T5):
+    return exact.checkerboard_kernel(L, J, 0, T5) @ exact.checkerboard_kernel(L, J, 1, T5)
+
+
+@pytest.mark.parametrize("L,q,J", [(2, 0.5, 0.8), (2, 0.6585, 0.6585), (3, 1.0, 0.4)])
+def test_cftp_samples_follow_the_stationary_law(orc, L, q, J):
+    """Propp-Wilson returns exact draws from the stationary law of the
+    quantised shaken chain (its stationary vector computed by enumeration);
+    every attempt coalesces well before the cap."""
+    M = 20000 if L == 2 else 30000
+    codes, ks = orc.cftp_many(orc.SHAKEN, L, q, J, seed=77, id0=0, M=M, k_max=16)
+    assert np.all(ks >= 0)
+    pi = exact.stationary(exact.shaken_kernel(L, q, J, orc.thresholds(q, J)))
+    counts = np.bincount(codes.astype(np.int64), minlength=2 ** (L * L))
+    assert _chi2_pvalue(counts, pi) > 1e-4
+
+
+def test_cftp_reuses_the_randomness_of_each_time(orc):
+    """Starting further in the past changes nothing once an attempt has
+    coalesced: the time-0 state from -2^(k+3) equals the one from -2^k (the
+    step from -s to -s+1 always uses forward step index s - 1)."""
+    L, q, J = 32, 0.8, 0.35
+    k, s = orc.cftp(orc.SHAKEN, L, q, J, 5, 3, k_max=14)
+    assert k >= 0
+    for start in (2 ** k, 2 ** (k + 3)):
+        top_s, top_t = np.ones(L * L, np.int8), np.ones(L * L, np.int8)
+        bot_s, bot_t = -np.ones(L * L, np.int8), -np.ones(L * L, np.int8)
+        for sidx in range(start, 0, -1):
+            orc.run(top_s, top_t, L, q, J, 5, 3, sidx - 1, 1, want_obs=False)
+            orc.run(bot_s, bot_t, L, q, J, 5, 3, sidx - 1, 1, want_obs=False)
+        assert np.array_equal(top_s, s) and np.array_equal(bot_s, s)
+    if k > 0:   # the attempt before the successful one had not coalesced
+        top_s, top_t = np.ones(L * L, np.int8), np.ones(L * L, np.int8)
+        bot_s, bot_t = -np.ones(L * L, np.int8), -np.ones(L * L, np.int8)
+        for sidx in range(2 ** (k - 1), 0, -1):
+            orc.run(top_s, top_t, L, q, J, 5, 3, sidx - 1, 1, want_obs=False)
+            orc.run(bot_s, bot_t, L, q, J, 5, 3, sidx - 1, 1, want_obs=False)
+        assert not np.array_equal(top_s, bot_s)
+
+
+def test_cftp_checkerboard_follows_the_quantised_gibbs_law_2x2(orc):
+    L, J, M = 2, 0.6, 20000
+    T5 = orc.checkerboard_thresholds(J)
+    pi = exact.stationary(_quantised_checkerboard_step(L, J, T5))
+    assert np.max(np.abs(pi - exact.square_gibbs(L, J))) < 1e-8
+    codes, ks = orc.cftp_many(orc.CHECKERBOARD, L, 0.0, J, seed=31, id0=0, M=M, k_max=16)
+    assert np.all(ks >= 0)
+    assert _chi2_pvalue(np.bincount(codes.astype(np.int64), minlength=16), pi) > 1e-4
+
+
+def test_cftp_checkerboard_4x4_magnetisation_energy_law(orc):
+    """Perfect samples of the 4x4 checkerboard chain against the exact Gibbs
+    law of (magnetisation, energy) near the critical coupling."""
+    L, J, M = 4, 0.44, 12000
+    S = exact.spin_table(16)
+    pi = exact.square_gibbs(L, J)
+    up, right, _, _ = exact.neighbours(L)
+    key = (S.sum(axis=1) + 16) * 100 + (np.sum(S * (S[:, up] + S[:, right]), axis=1) + 40)
+    keys, inv = np.unique(key, return_inverse=True)
+    probs = np.bincount(inv, weights=pi, minlength=keys.size)
+    codes, ks = orc.cftp_many(orc.CHECKERBOARD, L, 0.0, J, seed=8, id0=0, M=M, k_max=18)
+    assert np.all(ks >= 0)
+    counts = np.bincount(inv[codes.astype(np.int64)], minlength=keys.size)
+    assert _chi2_pvalue(counts, probs) > 1e-4
