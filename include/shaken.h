@@ -171,19 +171,6 @@ int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
  * zeroes it).  Asynchronous. */
 int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags, int64_t* out, void* stream);
 
-/* Coalescence times (Section 3.2): for each pair, two copies of the chain
- * on an L x L torus (32 <= L <= 256, L % 32 == 0), one from all +1 and one
- * from all -1, driven by the same random numbers (seed, lattice id, steps).
- * The dynamics preserves the order, so they sandwich every other start, and
- * once the sigma planes agree they agree forever.  host_T[i] receives the
- * first n <= max_steps with sigma_top(n) == sigma_bottom(n), or max_steps + 1
- * if they never met.  dev_scratch: shk_coalescence_scratch_bytes(n_pairs)
- * device bytes owned by the caller.  Synchronous (waits for the result). */
-size_t shk_coalescence_scratch_bytes(int n_pairs);
-int shk_coalescence_times(int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
-                          const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch, size_t bytes,
-                          uint64_t* host_T, void* stream);
-
 /* The comparison dynamics of Section 3.2 for the square-lattice Ising model
  * H_G(s) = -J sum_x s_x (s_{x up} + s_{x right}) (the paper's parallel heat
  * bath on odd and even sites, whose stationary law is the Gibbs measure):
@@ -198,6 +185,44 @@ int shk_coalescence_times(int n_pairs, const int* L, const double* q, const doub
 int shk_checkerboard_thresholds(double J, uint32_t out[5]);
 int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
                          uint64_t n_steps, int64_t* dev_obs, void* stream);
+
+/* Dynamics selectors of the coalescence and coupling-from-the-past calls:
+ * the shaken dynamics (parameters q, J) and the checkerboard heat bath above
+ * (parameter J; q ignored, may be NULL). */
+#define SHK_DYN_SHAKEN 0
+#define SHK_DYN_CHECKERBOARD 1
+#define SHK_CFTP_MAX_K 20
+
+/* Coalescence times (Section 3.2): for each pair, two copies of the chain
+ * on an L x L torus (32 <= L <= 256, L % 32 == 0), one from all +1 and one
+ * from all -1, driven by the same random numbers (seed, lattice id, steps).
+ * Both dynamics preserve the order for J, q >= 0, so the two copies sandwich
+ * every other start, and once the sigma planes agree they agree forever.
+ * host_T[i] receives the first n <= max_steps with
+ * sigma_top(n) == sigma_bottom(n), or max_steps + 1 if they never met.
+ * dev_scratch: shk_coalescence_scratch_bytes(n_pairs) device bytes owned by
+ * the caller.  Synchronous (waits for the result). */
+size_t shk_coalescence_scratch_bytes(int n_pairs);
+int shk_coalescence_times(int dynamics, int n_pairs, const int* L, const double* q, const double* J,
+                          const uint64_t* seed, const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch,
+                          size_t bytes, uint64_t* host_T, void* stream);
+
+/* Perfect samples by coupling from the past (Propp-Wilson, Section 3.2), for
+ * the same pairs as shk_coalescence_times.  The step from time -s to -s + 1
+ * (s >= 1) uses the random numbers of forward step index s - 1, whatever the
+ * starting time.  Attempt k = 0, 1, ..., k_max runs the all +1 and all -1
+ * chains from time -2^k to 0; the first attempt after which their sigma planes
+ * agree gives the sample.  host_k[i] receives that k, or -1 when no attempt
+ * up to k_max (<= SHK_CFTP_MAX_K) coalesced.  dev_samples: device buffer of
+ * n_pairs samples, sample_stride_bytes apart (a multiple of 4, at least
+ * L^2 / 8 for the largest L, 4-byte aligned); sample i receives the
+ * bit-packed sigma at time 0 (zero when host_k[i] is -1).  dev_scratch:
+ * shk_cftp_scratch_bytes(n_pairs) device bytes.  Synchronous.  Exact draws
+ * from the stationary law need J, q >= 0 (the monotone case). */
+size_t shk_cftp_scratch_bytes(int n_pairs);
+int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
+             const uint32_t* lattice_id, int k_max, void* dev_samples, size_t sample_stride_bytes,
+             void* dev_scratch, size_t bytes, int32_t* host_k, void* stream);
 
 /* ------------------------------------------------------------ lattice handle */
 

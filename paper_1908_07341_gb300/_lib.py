@@ -20,6 +20,8 @@ INIT_ALL_UP, INIT_ALL_DOWN, INIT_RANDOM = 0, 1, 2
 HALF_A, HALF_B = 0, 1
 NOBS = 5
 NSTATS = 11
+DYN_SHAKEN, DYN_CHECKERBOARD = 0, 1
+CFTP_MAX_K = 20
 MAX_L = 262144
 MAX_STEP = 0x80000000
 
@@ -41,7 +43,9 @@ SIGNATURES = {
     "shk_set_sweep_variant": (_i, [_i, _i]),
     "shk_diag_correlations": (_i, [_vp, _i, _vp, _i, _vp, _vp]),
     "shk_coalescence_scratch_bytes": (_sz, [_i]),
-    "shk_coalescence_times": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp, _vp]),
+    "shk_coalescence_times": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp, _vp]),
+    "shk_cftp_scratch_bytes": (_sz, [_i]),
+    "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),
     "shk_checkerboard_thresholds": (_i, [_d, _vp]),
     "shk_checkerboard_run": (_i, [_vp, _i, _d, _u64, _u32, _u64, _u64, _vp, _vp]),
     "shk_init_plane": (_i, [_i, _vp, _i, _i, _u64, _u32, _u32, _vp]),

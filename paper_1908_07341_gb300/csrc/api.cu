@@ -228,6 +228,17 @@ int shk_checkerboard_thresholds(double J, uint32_t out[5]) {
     return SHK_OK;
 }
 
+// The checkerboard draw folded onto the three-class machinery: a six-entry
+// table whose upper half is (T[2], T[3], T[4]) and whose lower half is its
+// complement, with the checkerboard stream domain 2.
+static bool checkerboard_draw_params(double J, uint64_t seed, uint32_t lattice_id, DrawParams* P) {
+    uint32_t T5[5];
+    if (!std::isfinite(J)) return false;
+    for (int n = 0; n < 5; ++n) T5[n] = threshold_of(J * (double)(2 * n - 4));
+    const uint32_t T6[6] = {0u - T5[4], 0u - T5[3], 0u - T5[2], T5[2], T5[3], T5[4]};
+    return make_draw_params(seed, lattice_id, T6, 2u, P);
+}
+
 int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
                          uint64_t n_steps, int64_t* dev_obs, void* stream) {
     Geometry g;
@@ -235,11 +246,9 @@ int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t l
         return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
     if (plane == nullptr) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: plane is NULL");
     if (t0 + n_steps > SHK_MAX_STEP) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: step index would exceed 2^31");
-    uint32_t T5[5];
-    if (shk_checkerboard_thresholds(J, T5) != SHK_OK) return SHK_EINVAL;
-    const uint32_t T6[6] = {0u - T5[4], 0u - T5[3], 0u - T5[2], T5[2], T5[3], T5[4]};
     DrawParams P;
-    make_draw_params(seed, lattice_id, T6, 2u, &P);
+    if (!checkerboard_draw_params(J, seed, lattice_id, &P))
+        return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: J must be finite");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (dev_obs) {
         const cudaError_t e = cudaMemsetAsync(dev_obs, 0, (size_t)n_steps * 2 * sizeof(int64_t), st);
@@ -255,44 +264,103 @@ int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t l
     return SHK_OK;
 }
 
-size_t shk_coalescence_scratch_bytes(int n_pairs) {
-    if (n_pairs <= 0) return 0;
-    return (((size_t)n_pairs * coalesce_pair_bytes() + 255) & ~(size_t)255) + (size_t)n_pairs * 8;
+// Validates the pairs of shk_coalescence_times / shk_cftp and writes their
+// descriptors to host; returns SHK_OK and the largest L, or an error.
+static int build_pairs(const char* who, int dynamics, int n_pairs, const int* L, const double* q,
+                       const double* J, const uint64_t* seed, const uint32_t* lattice_id,
+                       std::vector<unsigned char>& host, int* max_L) {
+    if (dynamics != SHK_DYN_SHAKEN && dynamics != SHK_DYN_CHECKERBOARD)
+        return fail(nullptr, SHK_EINVAL, "%s: unknown dynamics %d", who, dynamics);
+    if (n_pairs <= 0 || !L || !J || !seed || !lattice_id || (dynamics == SHK_DYN_SHAKEN && !q))
+        return fail(nullptr, SHK_EINVAL, "%s: bad argument", who);
+    host.assign((size_t)n_pairs * coalesce_pair_bytes(), 0);
+    *max_L = 32;
+    for (int i = 0; i < n_pairs; ++i) {
+        if (L[i] < 32 || L[i] > 256 || L[i] % 32 != 0)
+            return fail(nullptr, SHK_EINVAL, "%s: pair %d has L=%d (need 32..256, L %% 32 == 0)", who, i, L[i]);
+        DrawParams P;
+        bool ok;
+        if (dynamics == SHK_DYN_SHAKEN) {
+            uint32_t T[6];
+            ok = host_thresholds(q[i], J[i], T) == SHK_OK && make_draw_params(seed[i], lattice_id[i], T, 0u, &P);
+        } else {
+            ok = checkerboard_draw_params(J[i], seed[i], lattice_id[i], &P);
+        }
+        if (!ok) return fail(nullptr, SHK_EINVAL, "%s: pair %d has non-finite parameters", who, i);
+        fill_coalesce_pair(host.data() + (size_t)i * coalesce_pair_bytes(), L[i], P);
+        *max_L = std::max(*max_L, L[i]);
+    }
+    return SHK_OK;
 }
 
-int shk_coalescence_times(int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
-                          const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch, size_t bytes,
-                          uint64_t* host_T, void* stream) {
-    if (n_pairs <= 0 || !L || !q || !J || !seed || !lattice_id || !dev_scratch || !host_T)
-        return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: bad argument");
+static size_t pairs_bytes_aligned(int n_pairs) {
+    return ((size_t)n_pairs * coalesce_pair_bytes() + 255) & ~(size_t)255;
+}
+
+size_t shk_coalescence_scratch_bytes(int n_pairs) {
+    if (n_pairs <= 0) return 0;
+    return pairs_bytes_aligned(n_pairs) + (size_t)n_pairs * 8;
+}
+
+int shk_coalescence_times(int dynamics, int n_pairs, const int* L, const double* q, const double* J,
+                          const uint64_t* seed, const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch,
+                          size_t bytes, uint64_t* host_T, void* stream) {
+    if (!dev_scratch || !host_T) return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: bad argument");
+    if (max_steps == 0 || max_steps >= SHK_MAX_STEP)
+        return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: max_steps must be in 1..2^31-1");
+    std::vector<unsigned char> host;
+    int max_L = 32;
+    const int rc = build_pairs("shk_coalescence_times", dynamics, n_pairs, L, q, J, seed, lattice_id, host, &max_L);
+    if (rc != SHK_OK) return rc;
     if (bytes < shk_coalescence_scratch_bytes(n_pairs))
         return fail(nullptr, SHK_ENOMEM, "shk_coalescence_times: %zu bytes given, %zu needed", bytes,
                     shk_coalescence_scratch_bytes(n_pairs));
-    if (max_steps == 0 || max_steps >= SHK_MAX_STEP)
-        return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: max_steps must be in 1..2^31-1");
-    int max_L = 32;
-    std::vector<unsigned char> host((size_t)n_pairs * coalesce_pair_bytes());
-    for (int i = 0; i < n_pairs; ++i) {
-        if (L[i] < 32 || L[i] > 256 || L[i] % 32 != 0)
-            return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: pair %d has L=%d (need 32..256, L %% 32 == 0)",
-                        i, L[i]);
-        uint32_t T[6];
-        if (host_thresholds(q[i], J[i], T) != SHK_OK)
-            return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: pair %d has non-finite q or J", i);
-        DrawParams P;
-        make_draw_params(seed[i], lattice_id[i], T, 0u, &P);
-        fill_coalesce_pair(host.data() + (size_t)i * coalesce_pair_bytes(), L[i], P);
-        max_L = std::max(max_L, L[i]);
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* dev = static_cast<unsigned char*>(dev_scratch);
-    const size_t off_T = ((size_t)n_pairs * coalesce_pair_bytes() + 255) & ~(size_t)255;
+    const size_t off_T = pairs_bytes_aligned(n_pairs);
     cudaError_t e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = launch_coalesce(dev, (uint32_t)n_pairs, max_L, max_steps, reinterpret_cast<unsigned long long*>(dev + off_T), st);
+        e = launch_coalesce(dynamics, dev, (uint32_t)n_pairs, max_L, max_steps,
+                            reinterpret_cast<unsigned long long*>(dev + off_T), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_T, dev + off_T, (size_t)n_pairs * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_coalescence_times");
+    return SHK_OK;
+}
+
+size_t shk_cftp_scratch_bytes(int n_pairs) {
+    if (n_pairs <= 0) return 0;
+    return pairs_bytes_aligned(n_pairs) + (size_t)n_pairs * 4;
+}
+
+int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
+             const uint32_t* lattice_id, int k_max, void* dev_samples, size_t sample_stride_bytes,
+             void* dev_scratch, size_t bytes, int32_t* host_k, void* stream) {
+    if (!dev_samples || !dev_scratch || !host_k) return fail(nullptr, SHK_EINVAL, "shk_cftp: bad argument");
+    if (k_max < 0 || k_max > SHK_CFTP_MAX_K)
+        return fail(nullptr, SHK_EINVAL, "shk_cftp: k_max=%d outside 0..%d", k_max, SHK_CFTP_MAX_K);
+    std::vector<unsigned char> host;
+    int max_L = 32;
+    const int rc = build_pairs("shk_cftp", dynamics, n_pairs, L, q, J, seed, lattice_id, host, &max_L);
+    if (rc != SHK_OK) return rc;
+    if (sample_stride_bytes % 4 != 0 || sample_stride_bytes < (size_t)max_L * max_L / 8 ||
+        sample_stride_bytes / 4 > 0xffffffffull)
+        return fail(nullptr, SHK_EINVAL, "shk_cftp: sample stride %zu must be a multiple of 4 and >= %d",
+                    sample_stride_bytes, max_L * max_L / 8);
+    if ((reinterpret_cast<uintptr_t>(dev_samples) & 3u) != 0)
+        return fail(nullptr, SHK_EINVAL, "shk_cftp: dev_samples must be 4-byte aligned");
+    if (bytes < shk_cftp_scratch_bytes(n_pairs))
+        return fail(nullptr, SHK_ENOMEM, "shk_cftp: %zu bytes given, %zu needed", bytes, shk_cftp_scratch_bytes(n_pairs));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* dev = static_cast<unsigned char*>(dev_scratch);
+    const size_t off_k = pairs_bytes_aligned(n_pairs);
+    cudaError_t e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = launch_cftp(dynamics, dev, (uint32_t)n_pairs, max_L, k_max, static_cast<uint32_t*>(dev_samples),
+                        (uint32_t)(sample_stride_bytes / 4), reinterpret_cast<int*>(dev + off_k), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_k, dev + off_k, (size_t)n_pairs * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_cftp");
     return SHK_OK;
 }
 

@@ -59,7 +59,10 @@ cudaError_t launch_diag_corr(const Geometry& g, const void* plane, const int* la
 size_t coalesce_smem_bytes(int L);
 size_t coalesce_pair_bytes();
 void fill_coalesce_pair(void* dst, int L, const DrawParams& P);
-cudaError_t launch_coalesce(const void* pairs, uint32_t n_pairs, int max_L, uint64_t max_steps,
+constexpr int kDynShaken = 0, kDynCheckerboard = 1;
+cudaError_t launch_cftp(int dyn, const void* pairs, uint32_t n_pairs, int max_L, int k_max, uint32_t* samples,
+                        uint32_t sample_words, int* k_out, cudaStream_t st);
+cudaError_t launch_coalesce(int dyn, const void* pairs, uint32_t n_pairs, int max_L, uint64_t max_steps,
                             unsigned long long* T, cudaStream_t st);
 
 // Checkerboard heat-bath half-step in place on a bit-packed plane; after the

@@ -74,32 +74,64 @@ def init_plane(layout, plane: torch.Tensor, L: int, kind="random", init_seed: in
                                int(init_seed), int(lattice_id), int(plane_index), _stream_ptr(stream)))
 
 
-def diag_correlations(plane: torch.Tensor, L: int, lags, stream=None) -> torch.Tensor:
+def diag_correlations(plane: torch.Tensor, L: int, lags, stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
     """SW-NE and NW-SE spin sums of a bit-packed device plane for each lag
-    (int64 device tensor of 2 * len(lags): SW-NE first)."""
+    (int64 device tensor of 2 * len(lags): SW-NE first).  With `out` the sums
+    are added to it (accumulation over samples)."""
     lg = np.ascontiguousarray(lags, dtype=np.int32)
-    out = torch.zeros(2 * lg.size, dtype=torch.int64, device=plane.device)
+    if out is None:
+        out = torch.zeros(2 * lg.size, dtype=torch.int64, device=plane.device)
+    elif out.dtype != torch.int64 or out.numel() < 2 * lg.size or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int64 tensor of 2 * len(lags) entries")
     check(lib().shk_diag_correlations(plane.data_ptr(), int(L), lg.ctypes.data, int(lg.size), out.data_ptr(),
                                       _stream_ptr(stream)))
     return out
 
 
-def coalescence_times(L, q, J, seed, lattice_id, max_steps: int, device="cuda", stream=None) -> np.ndarray:
-    """Coalescence time of the all + and all - chains of every pair (see
-    shk_coalescence_times); max_steps + 1 where they did not meet."""
-    Ls = np.ascontiguousarray(L, dtype=np.int32)
+_DYN = {"shaken": 0, "checkerboard": 1}
+
+
+def _pair_arrays(L, q, J, seed, lattice_id):
+    Ls = np.ascontiguousarray(L, dtype=np.int32).reshape(-1)
     n = Ls.size
     qs = np.ascontiguousarray(np.broadcast_to(q, (n,)), dtype=np.float64)
     Js = np.ascontiguousarray(np.broadcast_to(J, (n,)), dtype=np.float64)
     ss = np.ascontiguousarray(np.broadcast_to(seed, (n,)), dtype=np.uint64)
     ids = np.ascontiguousarray(np.broadcast_to(lattice_id, (n,)), dtype=np.uint32)
+    return Ls, qs, Js, ss, ids
+
+
+def coalescence_times(L, q, J, seed, lattice_id, max_steps: int, device="cuda", stream=None,
+                      dynamics: str = "shaken") -> np.ndarray:
+    """Coalescence time of the all + and all - chains of every pair (see
+    shk_coalescence_times); max_steps + 1 where they did not meet.  dynamics:
+    "shaken" or "checkerboard" (q ignored)."""
+    Ls, qs, Js, ss, ids = _pair_arrays(L, q, J, seed, lattice_id)
+    n = Ls.size
     nbytes = int(lib().shk_coalescence_scratch_bytes(n))
     scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
     out = np.zeros(n, dtype=np.uint64)
-    check(lib().shk_coalescence_times(n, Ls.ctypes.data, qs.ctypes.data, Js.ctypes.data, ss.ctypes.data,
-                                      ids.ctypes.data, int(max_steps), scratch.data_ptr(), nbytes,
+    check(lib().shk_coalescence_times(_DYN[dynamics], n, Ls.ctypes.data, qs.ctypes.data, Js.ctypes.data,
+                                      ss.ctypes.data, ids.ctypes.data, int(max_steps), scratch.data_ptr(), nbytes,
                                       out.ctypes.data, _stream_ptr(stream)))
     return out
+
+
+def cftp(L, q, J, seed, lattice_id, k_max: int = 16, device="cuda", stream=None, dynamics: str = "shaken"):
+    """Perfect samples by coupling from the past (see shk_cftp).  Returns
+    (k, samples): k per pair (-1: not coalesced by k_max) and a uint8 device
+    tensor of shape (n, max L^2 / 8) holding each bit-packed sigma."""
+    Ls, qs, Js, ss, ids = _pair_arrays(L, q, J, seed, lattice_id)
+    n = Ls.size
+    stride = max(4, int(Ls.max()) ** 2 // 8)
+    samples = torch.empty((n, stride), dtype=torch.uint8, device=device)
+    nbytes = int(lib().shk_cftp_scratch_bytes(n))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    ks = np.zeros(n, dtype=np.int32)
+    check(lib().shk_cftp(_DYN[dynamics], n, Ls.ctypes.data, qs.ctypes.data, Js.ctypes.data, ss.ctypes.data,
+                         ids.ctypes.data, int(k_max), samples.data_ptr(), stride, scratch.data_ptr(), nbytes,
+                         ks.ctypes.data, _stream_ptr(stream)))
+    return ks, samples
 
 
 def checkerboard_thresholds(J: float) -> np.ndarray:

@@ -91,3 +91,58 @@ def test_checkerboard_resume_and_lattice_ids(orc):
     ref = s.copy()
     orc.checkerboard_run(ref, L, 0.5, 21, 1, 0, 12)
     assert np.array_equal(from_device_plane(c, L, "bitpack"), ref)
+
+
+# ---- coupling from the past and checkerboard coalescence
+
+from paper_1908_07341_gb300.lattice import cftp  # noqa: E402
+import paper_1908_07341_gb300 as _pkg  # noqa: E402,F401
+
+
+def _oracle_T_checkerboard(orc, L, J, seed, lat_id, max_steps):
+    top, bot = np.ones(L * L, np.int8), -np.ones(L * L, np.int8)
+    for t in range(max_steps):
+        orc.checkerboard_run(top, L, J, seed, lat_id, t, 1)
+        orc.checkerboard_run(bot, L, J, seed, lat_id, t, 1)
+        if np.array_equal(top, bot):
+            return t + 1
+    return max_steps + 1
+
+
+def test_checkerboard_coalescence_times_match_oracle(orc):
+    pairs = [(32, 0.3, 4, 0), (32, 0.4, 4, 1), (64, 0.35, 2, 2), (32, 0.1, 9, 3)]
+    L, J, seed, ids = (np.array(x) for x in zip(*pairs))
+    got = coalescence_times(L, 0.0, J, seed.astype(np.uint64), ids.astype(np.uint32), 1000,
+                            dynamics="checkerboard")
+    for k, (l_, j_, s_, i_) in enumerate(pairs):
+        assert int(got[k]) == _oracle_T_checkerboard(orc, l_, j_, s_, i_, 1000), pairs[k]
+
+
+def _unpack(samples, L):
+    from paper_1908_07341_gb300 import unpack_bits
+    return unpack_bits(samples[: L * L // 8], L).reshape(-1)
+
+
+@pytest.mark.parametrize("dyn", ["shaken", "checkerboard"])
+def test_cftp_matches_oracle(orc, dyn):
+    """k and the time-0 sample of every pair equal the oracle's coupling from
+    the past; pairs of different L share one launch."""
+    if dyn == "shaken":
+        pairs = [(32, 0.8, 0.35, 5, 3), (32, 1.0, 0.3, 6, 0), (64, 0.6585, 0.5, 2, 7), (32, 0.3, 0.2, 1, 1)]
+    else:
+        pairs = [(32, 0.0, 0.3, 5, 3), (32, 0.0, 0.35, 6, 0), (64, 0.0, 0.25, 2, 7)]
+    L, q, J, seed, ids = (np.array(x) for x in zip(*pairs))
+    ks, samples = cftp(L, q, J, seed.astype(np.uint64), ids.astype(np.uint32), k_max=14, dynamics=dyn)
+    host = samples.cpu().numpy()
+    code = orc.SHAKEN if dyn == "shaken" else orc.CHECKERBOARD
+    for i, (l_, q_, j_, s_, id_) in enumerate(pairs):
+        k_ref, s_ref = orc.cftp(code, int(l_), float(q_), float(j_), int(s_), int(id_), k_max=14)
+        assert int(ks[i]) == k_ref, pairs[i]
+        assert k_ref >= 0
+        assert np.array_equal(_unpack(host[i], int(l_)), s_ref), pairs[i]
+
+
+def test_cftp_reports_no_coalescence():
+    ks, samples = cftp([64], [2.0], [1.5], [3], [0], k_max=3)
+    assert int(ks[0]) == -1
+    assert int(samples.to(torch.int64).sum()) == 0
