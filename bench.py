@@ -98,6 +98,27 @@ def _expected_algorithmic_ops_per_block():
     return 40.0 * e_calls + 6.0 * e_planes, e_planes, e_calls
 
 
+def measure_philox_peak(dev, stream, iters: int = 16384, reps: int = 5) -> float:
+    """Philox4x32-10 calls per second of the library's own generator with no
+    memory traffic (shk_philox_peak: 8 CTAs of 256 threads per SM, independent
+    calls per thread), best of `reps` launches timed with events on `stream`."""
+    from paper_1908_07341_gb300 import _lib
+    so = _lib.lib()
+    out = torch.zeros(1, dtype=torch.int32, device=dev)
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    _lib.check(so.shk_philox_peak(blocks, iters, out.data_ptr(), stream.cuda_stream))
+    best = float("inf")
+    for _ in range(reps):
+        s_ev = torch.cuda.Event(enable_timing=True)
+        e_ev = torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        _lib.check(so.shk_philox_peak(blocks, iters, out.data_ptr(), stream.cuda_stream))
+        e_ev.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, s_ev.elapsed_time(e_ev))
+    return blocks * 256.0 * iters / (best / 1e3)
+
+
 # ----------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -320,6 +341,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     t_wall0 = time.perf_counter()
     ms, e2e, kern_ms = bench_layout("bitpack", args.steps, args.warmup, with_e2e=True)
     wall = time.perf_counter() - t_wall0
+    from paper_1908_07341_gb300 import tune as _tune
+    variant_bp = _tune.variant_names("bitpack")[_tune.get_variant("bitpack")]
     clocks = sampler.stop(tuple(window)) if sampler else None
 
     units_per_step = 2 * L * L * STEPS_PER_BENCH_STEP
@@ -328,6 +351,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # secondary line: the int8 layout on the same workload (fewer steps)
     ms8, _, kern8_ms = bench_layout("int8", max(2, args.steps // 5), 1, with_e2e=False)
+    variant_i8 = _tune.variant_names("int8")[_tune.get_variant("int8")]
     value8, _ = whole_job_rate(ms8, units_per_step * max(2, args.steps // 5), dist, dev)
 
     if rank != 0:
@@ -337,6 +361,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     hbm_gbs, sm_max, peak_kind = _peaks()
     ops_block, e_planes, e_calls = _expected_algorithmic_ops_per_block()
+    philox_cps = measure_philox_peak(dev, stream)
     sites_per_launch = L * L
     alu_ops = ops_block * (sites_per_launch / 32)
     alu_peak = SM_COUNT * 128 * sm_max * 1e6 / 1e12          # Tops/s, issue slots at max clock
@@ -358,18 +383,24 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "gpu_launches": args.steps * (2 * STEPS_PER_BENCH_STEP + 1),
         "roofline": {
             "bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Tops/s",
-            "frac": alu_achieved / alu_peak, "traffic": traffic.get("k_sweep_bp"),
-            "kernel": "k_sweep_q<bitpack> (half-step A/B, two-phase)", "kernel_ms": kern_ms,
+            "frac": alu_achieved / alu_peak, "traffic": traffic.get(f"bitpack:{variant_bp}"),
+            "kernel": f"bit-packed half-step A/B, launch shape {variant_bp}", "kernel_ms": kern_ms,
             "peak_basis": f"{SM_COUNT} SMs x 128 issue lanes x {sm_max:.0f} MHz (derived)",
             "algorithmic_ops_per_32_sites": ops_block,
             "hbm": {"achieved": hbm_bytes_bp / (kern_ms / 1e3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
                     "frac": hbm_bytes_bp / (kern_ms / 1e3) / 1e9 / hbm_gbs, "peak_kind": peak_kind},
+            "philox": {"calls_per_s": philox_cps, "expected_calls_per_32_sites": e_calls,
+                       "ceiling": philox_cps * 32.0 / e_calls,
+                       "achieved": sites_per_launch / (kern_ms / 1e3), "unit": "site updates/s",
+                       "frac": sites_per_launch / (kern_ms / 1e3) / (philox_cps * 32.0 / e_calls),
+                       "basis": "measured shk_philox_peak x 32 sites / expected Philox calls per block"},
         },
         "int8": {"value": value8, "unit": UNIT, "steps": max(2, args.steps // 5),
                  "roofline": {"bound": "hbm", "achieved": hbm_bytes_i8 / (kern8_ms / 1e3) / 1e9,
                               "peak": hbm_gbs, "unit": "GB/s",
                               "frac": hbm_bytes_i8 / (kern8_ms / 1e3) / 1e9 / hbm_gbs,
-                              "traffic": traffic.get("k_sweep_strip_int8"), "kernel_ms": kern8_ms,
+                              "traffic": traffic.get(f"int8:{variant_i8}"), "kernel_ms": kern8_ms,
+                              "kernel": f"int8 half-step A/B, launch shape {variant_i8}",
                               "peak_kind": peak_kind}},
         "clocks": clocks,
         "wall_s_bitpack": wall,
@@ -483,9 +514,11 @@ def bench_serving(dev, stream, n_jobs: int = 200, steps_per_launch: int = 2, lau
 
 
 def run_kernel_case(spec: str) -> int:
-    """--kernel-case LAYOUT:L:LAUNCHES -- a random-start lattice and LAUNCHES
-    alternating half-step launches through shk_halfstep (the benchmark's
-    kernel and grid), nothing else: the command profiled in profiles/."""
+    """--kernel-case LAYOUT:L:LAUNCHES[:VARIANT] -- a random-start lattice and
+    LAUNCHES alternating half-step launches through shk_halfstep (the
+    benchmark's kernel and grid), nothing else: the command profiled in
+    profiles/.  Without VARIANT the launch shape is autotuned first (which
+    launches every variant); with it that variant is set directly."""
     import torch
 
     from paper_1908_07341_gb300 import build as libbuild
@@ -493,10 +526,13 @@ def run_kernel_case(spec: str) -> int:
     libbuild.build()
     import paper_1908_07341_gb300 as shk
 
-    layout, side, launches = spec.split(":")
-    side, launches = int(side), int(launches)
+    parts = spec.split(":")
+    layout, side, launches = parts[0], int(parts[1]), int(parts[2])
     from paper_1908_07341_gb300 import tune
-    tune.autotune(layout, side)                  # the launch shape the benchmark uses
+    if len(parts) > 3:
+        tune.set_variant(layout, int(parts[3]))
+    else:
+        tune.autotune(layout, side)              # the launch shape the benchmark uses
     lat = shk.Lattice(side, layout).set_seed(SEED, 0).set_params(Q, J).init("random", init_seed=INIT_SEED)
     T = shk.thresholds(Q, J)
     acc = torch.zeros(shk.NOBS, dtype=torch.int64, device="cuda")
@@ -509,9 +545,11 @@ def run_kernel_case(spec: str) -> int:
     return 0
 
 
-def run_batch_case(n_lattices: int) -> int:
-    """--batch-case N -- the first N lattices of the phase-diagram workload,
-    autotuned, then 8 launches: the command profiled for k_batch."""
+def run_batch_case(spec: str) -> int:
+    """--batch-case N[:K:BLOCK:TILE] -- the first N lattices of the
+    phase-diagram workload, autotuned (or configured with K steps per launch,
+    BLOCK threads and TILE sites when given), then 8 launches: the command
+    profiled for k_batch."""
     import torch
 
     from paper_1908_07341_gb300 import build as libbuild
@@ -520,10 +558,16 @@ def run_batch_case(n_lattices: int) -> int:
     from paper_1908_07341_gb300 import tune, workloads
     from paper_1908_07341_gb300.batch import Batch
 
+    parts = [int(x) for x in str(spec).split(":")]
+    n_lattices = parts[0]
     w = workloads.phase_diagram_batch()
     sel = {k: w[k][:n_lattices] for k in ("L", "q", "J", "seed", "lattice_id")}
     b = Batch(**sel)
-    best = tune.autotune_batch(b, init_kind="random", init_seed=w["init_seed"])["best"]
+    if len(parts) == 4:
+        best = tuple(parts[1:])
+        b.configure(*best).init("random", w["init_seed"])
+    else:
+        best = tune.autotune_batch(b, init_kind="random", init_seed=w["init_seed"])["best"]
     b.run(8 * best[0])
     torch.cuda.synchronize()
     print(json.dumps({"batch_case": n_lattices, "tuned": list(best), "step": b.step}))
@@ -534,7 +578,7 @@ def _kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("device.cuh", "kernels.cu", "batch.cu"):
+    for f in ("device.cuh", "sweep.cuh", "kernels.cu", "batch.cu"):
         with open(os.path.join(ROOT, "paper_1908_07341_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -567,10 +611,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving line")
     ap.add_argument("--serving-jobs", type=int, default=200,
                     help="jobs of the serving stream to replay (10000 = the full stream)")
-    ap.add_argument("--batch-case", type=int, default=0,
-                    help="N -- only run the first N phase-diagram lattices (for profiling)")
+    ap.add_argument("--batch-case", default=None,
+                    help="N[:K:BLOCK:TILE] -- only run the first N phase-diagram lattices (for profiling)")
     ap.add_argument("--kernel-case", default=None,
-                    help="LAYOUT:L:LAUNCHES -- only run half-step launches (for profiling)")
+                    help="LAYOUT:L:LAUNCHES[:VARIANT] -- only run half-step launches (for profiling)")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args.kernel_case)

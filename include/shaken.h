@@ -224,6 +224,13 @@ int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const dou
              const uint32_t* lattice_id, int k_max, void* dev_samples, size_t sample_stride_bytes,
              void* dev_scratch, size_t bytes, int32_t* host_k, void* stream);
 
+/* Measurement helper (no counterpart in the paper): blocks x 256 threads
+ * each run iters Philox4x32-10 calls of the half-step's generator with no
+ * memory traffic and XOR their outputs into *dev_out (device uint32).  The
+ * caller times the launch on its stream; blocks * 256 * iters / seconds is
+ * the measured Philox ceiling of the bit-packed draw.  Asynchronous. */
+int shk_philox_peak(int blocks, uint32_t iters, uint32_t* dev_out, void* stream);
+
 /* ------------------------------------------------------------ lattice handle */
 
 typedef struct shk_lattice shk_lattice;

@@ -45,6 +45,7 @@ SIGNATURES = {
     "shk_coalescence_scratch_bytes": (_sz, [_i]),
     "shk_coalescence_times": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp, _vp]),
     "shk_cftp_scratch_bytes": (_sz, [_i]),
+    "shk_philox_peak": (_i, [_i, _u32, _vp, _vp]),
     "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),
     "shk_checkerboard_thresholds": (_i, [_d, _vp]),
     "shk_checkerboard_run": (_i, [_vp, _i, _d, _u64, _u32, _u64, _u64, _vp, _vp]),

@@ -1,0 +1,425 @@
+// sampling.cu -- the Section 3 kernels on bit-packed planes and their
+// launchers:
+//   k_diag_corr          SW-NE / NW-SE spin-spin sums at up to eight lags
+//                        (Section 3.3, Table 1)
+//   k_checkerboard<P>    the square-lattice heat bath on the sites of one
+//                        parity (the comparison dynamics of Section 3.2)
+//   k_sq_obs             magnetisation and C_nn of a plane
+//   k_coalesce<DYN>      coalescence times of the all + / all - coupling
+//   k_cftp<DYN>          Propp-Wilson coupling from the past
+// The draw machinery (Philox, lazy bit-serial comparison) is the half-steps'
+// own (device.cuh).
+#include <algorithm>
+
+#include "internal.h"
+#include "sweep.cuh"
+
+namespace shk {
+
+// ------------------------------------------------------------ diagonal correlations
+
+constexpr int kMaxLags = 8;
+
+struct CorrArgs {
+    const uint32_t* plane;
+    uint32_t L, Wr, nblocks;
+    FastDiv div_row;
+    int n_lags;
+    uint32_t lag[kMaxLags];
+    long long* out;      // [0, n_lags): SW-NE sums, [n_lags, 2 n_lags): NW-SE sums
+};
+
+// Bits of sites (i + l .. i + l + 31, row) for the block whose first site is
+// i = 32 c, read from a bit-packed row with wrap-around.
+__device__ __forceinline__ uint32_t shifted_row_word(const uint32_t* row, uint32_t c, uint32_t l, uint32_t Wr) {
+    const uint32_t cw = (c + (l >> 5)) % Wr;
+    const uint32_t sh = l & 31u;
+    const uint32_t lo = row[cw];
+    if (sh == 0) return lo;
+    const uint32_t hi = row[cw + 1 == Wr ? 0 : cw + 1];
+    return (lo >> sh) | (hi << (32u - sh));
+}
+
+// sum_x s_x s_{x+(l,l)} and sum_x s_x s_{x+(l,-l)} for every lag (Section
+// 3.3: the SW-NE pair (0,0)-(l,l) and the NW-SE pair (0,l)-(l,0), averaged
+// over translations of the torus).
+__global__ void __launch_bounds__(256) k_diag_corr(const CorrArgs a) {
+    int acc[2 * kMaxLags];
+#pragma unroll
+    for (int k = 0; k < 2 * kMaxLags; ++k) acc[k] = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
+        const uint32_t j = fdiv(w, a.div_row), c = w - j * a.Wr;
+        const uint32_t s = a.plane[w];
+#pragma unroll
+        for (int k = 0; k < kMaxLags; ++k) {
+            if (k < a.n_lags) {
+                const uint32_t l = a.lag[k];
+                const uint32_t jp = j + l >= a.L ? j + l - a.L : j + l;
+                const uint32_t jm = j >= l ? j - l : j + a.L - l;
+                const uint32_t p1 = shifted_row_word(a.plane + (size_t)jp * a.Wr, c, l, a.Wr);
+                const uint32_t p2 = shifted_row_word(a.plane + (size_t)jm * a.Wr, c, l, a.Wr);
+                acc[k] += 32 - 2 * __popc(s ^ p1);
+                acc[kMaxLags + k] += 32 - 2 * __popc(s ^ p2);
+            }
+        }
+    }
+    __shared__ long long red[2 * kMaxLags][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 2 * kMaxLags; ++k) {
+        const int v = warp_sum(acc[k]);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kMaxLags) {
+        const int k = threadIdx.x;
+        const int lk = k < kMaxLags ? k : k - kMaxLags;
+        if (lk < a.n_lags) {
+            long long t = 0;
+            for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[k][i];
+            const int idx = k < kMaxLags ? lk : a.n_lags + lk;
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.out + idx), (unsigned long long)t);
+        }
+    }
+}
+
+// ------------------------------------------------------------ checkerboard heat bath
+
+// The square-lattice comparison dynamics of Section 3.2: the sites with
+// (i + j) % 2 == parity are redrawn in place, P(+1) = e^h / (2 cosh h) with
+// h = J (2n - 4), n the number of + among the four neighbours (all of the
+// other parity, so unchanged while the parity is redrawn).  With the
+// complement rule the five thresholds fold onto the three-class draw: sites
+// with n < 2 compare their complemented uniform, and the class is
+// n' = max(n, 4 - n) - 2 with thresholds (T[2], T[3], T[4]).  Returns the
+// classes of block w (row, col) of a bit-packed plane and sets pm to the mask
+// of its sites of the given parity.
+__device__ __forceinline__ BlockClass checkerboard_class(const uint32_t* pl, uint32_t w, uint32_t row,
+                                                         uint32_t col, uint32_t L, uint32_t Wr,
+                                                         uint32_t nblocks, uint32_t parity, uint32_t& pm) {
+    const uint32_t S = pl[w];
+    const uint32_t U = pl[row + 1 < L ? w + Wr : w + Wr - nblocks];
+    const uint32_t D = pl[row > 0 ? w - Wr : w + nblocks - Wr];
+    const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
+    const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
+    const uint32_t Lf = (S << 1) | (prev >> 31);
+    const uint32_t Rt = (S >> 1) | (next << 31);
+    // n = U + D + Lf + Rt per site, as bits b0 + 2 b1 + 4 b2
+    const uint32_t ab_s = U ^ D, ab_c = U & D, cd_s = Lf ^ Rt, cd_c = Lf & Rt;
+    const uint32_t b0 = ab_s ^ cd_s, c0 = ab_s & cd_s;
+    const uint32_t b1 = ab_c ^ cd_c ^ c0;
+    const uint32_t b2 = (ab_c & cd_c) | ((ab_c ^ cd_c) & c0);
+    const uint32_t extreme = b2 | ~(b0 | b1 | b2);       // n == 4 or n == 0
+    pm = ((row & 1u) == parity) ? 0x55555555u : 0xAAAAAAAAu;
+    BlockClass k;
+    k.F = ~(b1 | b2);                                   // n < 2
+    k.C2 = extreme;
+    k.Cg = b0 | extreme;                                // n odd or extreme
+    return k;
+}
+
+template <int PARITY>
+__global__ void __launch_bounds__(256) k_checkerboard(const SweepArgs a) {
+    uint32_t* pl = static_cast<uint32_t*>(a.dst);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
+        const uint32_t w = base + lane;
+        const uint32_t row = fdiv(w, a.div_row);
+        uint32_t pm;
+        const BlockClass k = checkerboard_class(pl, w, row, w - row * a.Wr, a.L, a.Wr, a.nblocks, PARITY, pm);
+        const uint32_t S = pl[w];
+        const uint32_t up = draw_block_class(k, w, pm, a.hs, a.P);
+        pl[w] = (S & ~pm) | (up & pm);
+    }
+}
+
+// ------------------------------------------------------------ coalescence and coupling from the past
+
+struct CoalescePair {
+    uint32_t L, Wr, nblocks;
+    uint32_t pad;
+    DrawParams P;
+};
+
+struct CoalesceArgs {
+    const CoalescePair* pairs;
+    uint32_t n_pairs;
+    unsigned long long max_steps;
+    unsigned long long* T;      // per pair: first n with sigma_top == sigma_bottom, or max_steps + 1
+};
+
+struct CftpArgs {
+    const CoalescePair* pairs;
+    uint32_t n_pairs;
+    int k_max;
+    uint32_t* samples;          // per pair: sample_words words (the sigma plane at time 0)
+    uint32_t sample_words;
+    int* k_out;                 // per pair: k of the successful attempt, or -1
+};
+
+// Bits of block w and of its two field neighbours in a bit-packed shared-
+// memory plane (rows of Wr words, L rows, wrapping).
+template <int HALF>
+__device__ __forceinline__ void smem_fields(const uint32_t* pl, uint32_t w, uint32_t Wr, uint32_t L,
+                                            uint32_t nblocks, uint32_t& S, uint32_t& N1, uint32_t& N2) {
+    const uint32_t row = w / Wr, col = w - row * Wr;
+    words_aligned<HALF>(pl, w, row, col, L, Wr, nblocks, S, N1, N2);
+}
+
+// Four bit-packed planes of one CTA: sigma and tau of the chain started from
+// all + (top) and of the one started from all - (bottom).
+struct PairPlanes {
+    uint32_t *st, *tt, *sb, *tb;
+    uint32_t nb, nbp, Wr, L;
+};
+
+__device__ __forceinline__ PairPlanes pair_planes(uint32_t* smem, const CoalescePair& cp) {
+    PairPlanes p;
+    p.nb = cp.nblocks;
+    p.nbp = (cp.nblocks + 31u) & ~31u;
+    p.Wr = cp.Wr;
+    p.L = cp.L;
+    p.st = smem;
+    p.tt = smem + p.nbp;
+    p.sb = smem + 2 * p.nbp;
+    p.tb = smem + 3 * p.nbp;
+    return p;
+}
+
+__device__ __forceinline__ void pair_reset(const PairPlanes& p) {
+    for (uint32_t w = threadIdx.x; w < p.nbp; w += blockDim.x) {
+        p.st[w] = w < p.nb ? 0xffffffffu : 0u;
+        p.sb[w] = 0u;
+        p.tt[w] = p.tb[w] = 0u;
+    }
+    __syncthreads();
+}
+
+// One full step with index t of both chains, driven by the same uniforms
+// (shaken: half-steps A and B; checkerboard: even then odd sites of sigma).
+template <int DYN>
+__device__ __forceinline__ void pair_step(const PairPlanes& p, unsigned long long t, const DrawParams& P) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t hs = (uint32_t)(2 * t);
+    for (int half = 0; half < 2; ++half) {
+        for (uint32_t base = warp * 32; base < p.nbp; base += nwarps * 32) {
+            const uint32_t w = base + lane;
+            const bool in = w < p.nb;
+            if (DYN == kDynShaken) {
+                uint32_t S0 = 0, A0 = 0, B0 = 0, S1 = 0, A1 = 0, B1 = 0;
+                if (in) {
+                    if (half == 0) {
+                        smem_fields<0>(p.st, w, p.Wr, p.L, p.nb, S0, A0, B0);
+                        smem_fields<0>(p.sb, w, p.Wr, p.L, p.nb, S1, A1, B1);
+                    } else {
+                        smem_fields<1>(p.tt, w, p.Wr, p.L, p.nb, S0, A0, B0);
+                        smem_fields<1>(p.tb, w, p.Wr, p.L, p.nb, S1, A1, B1);
+                    }
+                }
+                const uint32_t S[2] = {S0, S1}, A[2] = {A0, A1}, B[2] = {B0, B1}, ww[2] = {w, w};
+                const uint32_t v[2] = {in ? 0xffffffffu : 0u, in ? 0xffffffffu : 0u};
+                uint32_t up[2];
+                draw_blocks<2>(S, A, B, ww, v, hs + (uint32_t)half, P, up);
+                if (in) {
+                    if (half == 0) {
+                        p.tt[w] = up[0];
+                        p.tb[w] = up[1];
+                    } else {
+                        p.st[w] = up[0];
+                        p.sb[w] = up[1];
+                    }
+                }
+            } else {
+                // in place: the words read for the neighbour counts keep the
+                // bits of the other parity, which no lane changes now
+                uint32_t* planes2[2] = {p.st, p.sb};
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t* pl = planes2[c];
+                    BlockClass k = {0u, 0u, 0u};
+                    uint32_t pm = 0u, S = 0u;
+                    if (in) {
+                        const uint32_t row = w / p.Wr;
+                        k = checkerboard_class(pl, w, row, w - row * p.Wr, p.L, p.Wr, p.nb, (uint32_t)half, pm);
+                        S = pl[w];
+                    }
+                    const uint32_t up = draw_block_class(k, w, pm, hs + (uint32_t)half, P);
+                    if (in) pl[w] = (S & ~pm) | (up & pm);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ bool pair_equal(const PairPlanes& p) {
+    uint32_t diff = 0;
+    for (uint32_t w = threadIdx.x; w < p.nb; w += blockDim.x) diff |= p.st[w] ^ p.sb[w];
+    return !__syncthreads_or(diff != 0u);
+}
+
+// Section 3.2: two copies of the chain, from all + (top) and all - (bottom),
+// driven by the same random numbers (the same seed, lattice id and steps).
+// The order is preserved, and once the sigma planes agree they agree forever;
+// T is the first step count n with sigma_top(n) == sigma_bottom(n).  One CTA
+// per pair, all four planes in shared memory.
+template <int DYN>
+__global__ void __launch_bounds__(256) k_coalesce(const CoalesceArgs a) {
+    extern __shared__ uint32_t planes[];
+    const uint32_t pi = blockIdx.x;
+    if (pi >= a.n_pairs) return;
+    const CoalescePair& cp = a.pairs[pi];
+    const PairPlanes p = pair_planes(planes, cp);
+    pair_reset(p);
+    unsigned long long T = a.max_steps + 1;
+    for (unsigned long long t = 0; t < a.max_steps; ++t) {
+        pair_step<DYN>(p, t, cp.P);
+        if (pair_equal(p)) {
+            T = t + 1;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) a.T[pi] = T;
+}
+
+// Propp-Wilson coupling from the past (Section 3.2).  The step from time -s
+// to -s + 1 always uses forward step index s - 1, so every attempt reuses the
+// randomness of the times it shares with the previous one.  Attempt k runs
+// both chains from -2^k to 0; the first one after which their sigma planes
+// agree gives the sample (its sigma at time 0) and k.  One CTA per pair.
+template <int DYN>
+__global__ void __launch_bounds__(256) k_cftp(const CftpArgs a) {
+    extern __shared__ uint32_t planes[];
+    const uint32_t pi = blockIdx.x;
+    if (pi >= a.n_pairs) return;
+    const CoalescePair& cp = a.pairs[pi];
+    const PairPlanes p = pair_planes(planes, cp);
+    int result = -1;
+    for (int k = 0; k <= a.k_max; ++k) {
+        pair_reset(p);
+        for (unsigned long long s = 1ull << k; s >= 1; --s) pair_step<DYN>(p, s - 1, cp.P);
+        if (pair_equal(p)) {
+            result = k;
+            break;
+        }
+    }
+    uint32_t* out = a.samples + (size_t)pi * a.sample_words;
+    for (uint32_t w = threadIdx.x; w < a.sample_words; w += blockDim.x)
+        out[w] = (result >= 0 && w < p.nb) ? p.st[w] : 0u;
+    if (threadIdx.x == 0) a.k_out[pi] = result;
+}
+
+// Magnetisation and C_nn = sum_x s_x (s_{x down} + s_{x left}) (equal by
+// translation to the up/right form) of a bit-packed plane, added to out[0..1].
+__global__ void __launch_bounds__(256) k_sq_obs(const SweepArgs a) {
+    int m = 0, c = 0;
+    const uint32_t* pl = static_cast<const uint32_t*>(a.src);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
+        const uint32_t row = fdiv(w, a.div_row);
+        uint32_t S, N1, N2;
+        words_aligned<0>(pl, w, row, w - row * a.Wr, a.L, a.Wr, a.nblocks, S, N1, N2);
+        m += 2 * __popc(S) - 32;
+        c += 64 - 2 * (__popc(S ^ N1) + __popc(S ^ N2));
+    }
+    const int v[2] = {m, c};
+    long long* const d[2] = {a.obs_cur, a.obs_cur ? a.obs_cur + 1 : nullptr};
+    block_accumulate<2>(v, d);
+}
+
+// ------------------------------------------------------------ host side
+
+cudaError_t launch_diag_corr(const Geometry& g, const void* plane, const int* lags, int n_lags, long long* out,
+                             cudaStream_t st) {
+    CorrArgs a;
+    a.plane = static_cast<const uint32_t*>(plane);
+    a.L = (uint32_t)g.L;
+    a.Wr = g.Wr;
+    a.nblocks = g.nblocks;
+    a.div_row = make_fastdiv(g.Wr);
+    a.n_lags = n_lags;
+    for (int k = 0; k < kMaxLags; ++k) a.lag[k] = k < n_lags ? (uint32_t)lags[k] : 0u;
+    a.out = out;
+    k_diag_corr<<<grid_for(k_diag_corr, 256, g.nblocks), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+size_t coalesce_smem_bytes(int L) { return 4 * (size_t)(((L * L / 32) + 31) & ~31) * 4; }
+
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t smem) {
+    if (smem > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
+
+cudaError_t launch_coalesce(int dyn, const void* pairs, uint32_t n_pairs, int max_L, uint64_t max_steps,
+                            unsigned long long* T, cudaStream_t st) {
+    CoalesceArgs a;
+    a.pairs = static_cast<const CoalescePair*>(pairs);
+    a.n_pairs = n_pairs;
+    a.max_steps = max_steps;
+    a.T = T;
+    const size_t smem = coalesce_smem_bytes(max_L);
+    cudaError_t e;
+    if (dyn == kDynShaken) {
+        e = allow_smem(k_coalesce<kDynShaken>, smem);
+        if (e == cudaSuccess) k_coalesce<kDynShaken><<<n_pairs, 256, smem, st>>>(a);
+    } else {
+        e = allow_smem(k_coalesce<kDynCheckerboard>, smem);
+        if (e == cudaSuccess) k_coalesce<kDynCheckerboard><<<n_pairs, 256, smem, st>>>(a);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+cudaError_t launch_cftp(int dyn, const void* pairs, uint32_t n_pairs, int max_L, int k_max, uint32_t* samples,
+                        uint32_t sample_words, int* k_out, cudaStream_t st) {
+    CftpArgs a;
+    a.pairs = static_cast<const CoalescePair*>(pairs);
+    a.n_pairs = n_pairs;
+    a.k_max = k_max;
+    a.samples = samples;
+    a.sample_words = sample_words;
+    a.k_out = k_out;
+    const size_t smem = coalesce_smem_bytes(max_L);
+    cudaError_t e;
+    if (dyn == kDynShaken) {
+        e = allow_smem(k_cftp<kDynShaken>, smem);
+        if (e == cudaSuccess) k_cftp<kDynShaken><<<n_pairs, 256, smem, st>>>(a);
+    } else {
+        e = allow_smem(k_cftp<kDynCheckerboard>, smem);
+        if (e == cudaSuccess) k_cftp<kDynCheckerboard><<<n_pairs, 256, smem, st>>>(a);
+    }
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+size_t coalesce_pair_bytes() { return sizeof(CoalescePair); }
+
+void fill_coalesce_pair(void* dst, int L, const DrawParams& P) {
+    CoalescePair* c = static_cast<CoalescePair*>(dst);
+    c->L = (uint32_t)L;
+    c->Wr = (uint32_t)L / 32;
+    c->nblocks = (uint32_t)((int64_t)L * L / 32);
+    c->pad = 0;
+    c->P = P;
+}
+
+cudaError_t launch_checkerboard(const Geometry& g, void* plane, const DrawParams& P, uint32_t hs, int parity,
+                                long long* obs, cudaStream_t st) {
+    SweepArgs a = sweep_args(g, plane, plane, P, hs, obs, nullptr, nullptr);
+    const int block = 256;
+    if (parity == 0) {
+        k_checkerboard<0><<<grid_for(k_checkerboard<0>, block, g.nblocks), block, 0, st>>>(a);
+    } else {
+        k_checkerboard<1><<<grid_for(k_checkerboard<1>, block, g.nblocks), block, 0, st>>>(a);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && obs != nullptr && parity == 1)
+        k_sq_obs<<<grid_for(k_sq_obs, block, g.nblocks), block, 0, st>>>(a);
+    return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+}  // namespace shk

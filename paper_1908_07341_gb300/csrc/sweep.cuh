@@ -1,0 +1,143 @@
+// sweep.cuh -- what the half-step sweeps (kernels.cu) and the Section 3
+// kernels (sampling.cu) share: the sweep arguments, the neighbour gathers of
+// a 32-site block, and the launch-grid helper.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace shk {
+
+struct SweepArgs {
+    const void* src;
+    void* dst;
+    uint32_t L;
+    uint32_t Wr;          // blocks per row (aligned layouts)
+    uint32_t nblocks;     // ceil(N / 32)
+    int64_t N;
+    FastDiv div_row;      // division by Wr
+    uint32_t hs;
+    long long* obs_cur;
+    long long* obs_prev;
+    long long* zero_slot;
+    DrawParams P;
+};
+
+// ------------------------------------------------------------ neighbour gathers
+
+// Bits of block w of a bit-packed (or bit-converted) plane and of the two field
+// neighbours of its sites: HALF 0 -> (x down, x left), HALF 1 -> (x up, x right).
+template <int HALF>
+__device__ __forceinline__ void words_aligned(const uint32_t* __restrict__ pl, uint32_t w,
+                                              uint32_t row, uint32_t col, uint32_t L, uint32_t Wr,
+                                              uint32_t nblocks, uint32_t& S, uint32_t& N1,
+                                              uint32_t& N2) {
+    S = pl[w];
+    if (HALF == 0) {
+        N1 = pl[row > 0 ? w - Wr : w + nblocks - Wr];
+        const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
+        N2 = (S << 1) | (prev >> 31);
+    } else {
+        N1 = pl[row + 1 < L ? w + Wr : w + Wr - nblocks];
+        const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
+        N2 = (S >> 1) | (next << 31);
+    }
+}
+
+__device__ __forceinline__ uint32_t bit_of(const uint32_t* pl, int64_t v) {
+    return (pl[v >> 5] >> (v & 31)) & 1u;
+}
+
+// Generic side length (L % 32 != 0): site-by-site neighbour bits of block w of
+// a bit plane with linear site order.
+template <int HALF>
+__device__ __forceinline__ void words_generic(const uint32_t* pl, uint32_t w, int64_t L, int64_t N,
+                                              uint32_t& S, uint32_t& N1, uint32_t& N2,
+                                              uint32_t& valid) {
+    S = N1 = N2 = valid = 0;
+    for (int p = 0; p < 32; ++p) {
+        const int64_t u = 32 * (int64_t)w + p;
+        if (u >= N) break;
+        const int64_t j = u / L, i = u - j * L;
+        int64_t a, b;
+        if (HALF == 0) {
+            a = j > 0 ? u - L : u + N - L;
+            b = i > 0 ? u - 1 : u + L - 1;
+        } else {
+            a = j + 1 < L ? u + L : u + L - N;
+            b = i + 1 < L ? u + 1 : u + 1 - L;
+        }
+        S |= bit_of(pl, u) << p;
+        N1 |= bit_of(pl, a) << p;
+        N2 |= bit_of(pl, b) << p;
+        valid |= 1u << p;
+    }
+}
+
+// int8 plane, generic L: site-by-site.
+template <int HALF>
+__device__ __forceinline__ void bytes_generic(const int8_t* __restrict__ pl, uint32_t w, int64_t L,
+                                              int64_t N, uint32_t& S, uint32_t& N1, uint32_t& N2,
+                                              uint32_t& valid) {
+    S = N1 = N2 = valid = 0;
+    for (int p = 0; p < 32; ++p) {
+        const int64_t u = 32 * (int64_t)w + p;
+        if (u >= N) break;
+        const int64_t j = u / L, i = u - j * L;
+        int64_t a, b;
+        if (HALF == 0) {
+            a = j > 0 ? u - L : u + N - L;
+            b = i > 0 ? u - 1 : u + L - 1;
+        } else {
+            a = j + 1 < L ? u + L : u + L - N;
+            b = i + 1 < L ? u + 1 : u + 1 - L;
+        }
+        S |= (uint32_t)(pl[u] > 0) << p;
+        N1 |= (uint32_t)(pl[a] > 0) << p;
+        N2 |= (uint32_t)(pl[b] > 0) << p;
+        valid |= 1u << p;
+    }
+}
+
+// int8 plane with L % 32 == 0: two 16-byte loads per 32 sites.
+template <int HALF>
+__device__ __forceinline__ void bytes_aligned(const int8_t* __restrict__ pl, uint32_t w, uint32_t row,
+                                              uint32_t col, uint32_t L, uint32_t Wr,
+                                              uint32_t nblocks, uint32_t& S, uint32_t& N1,
+                                              uint32_t& N2) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(pl + 32 * (size_t)w);
+    S = pack_up32(__ldg(s4), __ldg(s4 + 1));
+    uint32_t wn;
+    if (HALF == 0) wn = row > 0 ? w - Wr : w + nblocks - Wr;
+    else wn = row + 1 < L ? w + Wr : w + Wr - nblocks;
+    const uint4* n4 = reinterpret_cast<const uint4*>(pl + 32 * (size_t)wn);
+    N1 = pack_up32(__ldg(n4), __ldg(n4 + 1));
+    if (HALF == 0) {
+        const size_t idx = col > 0 ? 32 * (size_t)w - 1 : 32 * (size_t)w + L - 1;
+        N2 = (S << 1) | (uint32_t)(__ldg(pl + idx) > 0);
+    } else {
+        const size_t idx = col + 1 < Wr ? 32 * (size_t)w + 32 : 32 * (size_t)w + 32 - L;
+        N2 = (S >> 1) | ((uint32_t)(__ldg(pl + idx) > 0) << 31);
+    }
+}
+
+// ------------------------------------------------------------ host helpers
+
+int sm_count();
+int blocks_per_sm(const void* kernel, int block);
+SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawParams& P,
+                     uint32_t hs, long long* oc, long long* op, long long* z);
+
+// Grid of at most one full wave of resident blocks (the kernels stride over
+// their work), never more blocks than work items need.
+template <class K>
+inline int grid_for(K kernel, int block, uint64_t work_items) {
+    const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kernel), block);
+    const uint64_t full = (uint64_t)per_sm * sm_count();
+    const uint64_t need = (work_items + block - 1) / block;
+    return (int)std::max<uint64_t>(1, std::min(full, need));
+}
+
+}  // namespace shk

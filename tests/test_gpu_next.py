@@ -146,3 +146,22 @@ def test_cftp_reports_no_coalescence():
     ks, samples = cftp([64], [2.0], [1.5], [3], [0], k_max=3)
     assert int(ks[0]) == -1
     assert int(samples.to(torch.int64).sum()) == 0
+
+
+def test_philox_peak_kernel_computes_the_generator(orc):
+    """The measurement kernel runs the half-steps' Philox4x32-10: its XOR fold
+    over (block, thread, call) equals the oracle's fold of the same counters
+    (i, w, 0, 0) under the key 0x0123456789ABCDEF."""
+    from paper_1908_07341_gb300 import _lib
+    blocks, iters = 2, 3
+    out = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _lib.check(_lib.lib().shk_philox_peak(blocks, iters, out.data_ptr(), None))
+    torch.cuda.synchronize()
+    seed = 0x0123456789ABCDEF
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    ref = 0
+    for w in range(blocks * 256):
+        for i in range(iters):
+            r = orc.philox4x32_10([i, w, 0, 0], key)
+            ref ^= int(r[0]) ^ int(r[1]) ^ int(r[2]) ^ int(r[3])
+    assert int(out.item()) & 0xFFFFFFFF == ref

@@ -137,3 +137,10 @@ def test_checkerboard_argument_checks_without_gpu():
     out = (ctypes.c_uint32 * 5)()
     assert so.shk_checkerboard_thresholds(float("inf"), out) == _lib.EINVAL
     assert so.shk_checkerboard_thresholds(0.0, out) == _lib.OK and list(out) == [2 ** 31] * 5
+
+
+def test_philox_peak_argument_checks_without_gpu():
+    so = _lib.lib()
+    assert so.shk_philox_peak(0, 4, ctypes.c_void_p(16), None) == _lib.EINVAL
+    assert so.shk_philox_peak(4, 0, ctypes.c_void_p(16), None) == _lib.EINVAL
+    assert so.shk_philox_peak(4, 4, None, None) == _lib.EINVAL
