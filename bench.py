@@ -409,6 +409,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         line["batched"] = bench_batched(dev, stream)
     if not args.no_serving:
         line["serving"] = bench_serving(dev, stream, n_jobs=args.serving_jobs)
+    if not args.no_section3:
+        line["section3"] = bench_section3(dev, stream)
     if world == 1 and not args.no_cpu_baseline:
         rows = 8192
         rate, secs, units = _oracle_sample_rate(rows)
@@ -477,6 +479,66 @@ def bench_batched(dev, stream, plain_steps: int = 100):
             "plain_value": plain_rate, "plain_steps_timed": plain_steps, "plain_ms": plain_ms,
             "speedup_vs_plain": batched_rate / plain_rate, "tuned": list(tuned["best"]),
             "launches": w["steps"] // tuned["best"][0]}
+
+
+def bench_section3(dev, stream) -> dict:
+    """Throughput of the Section 3 kernels, each on a synthetic workload of
+    the paper's shape, timed with events on `stream` after a warm-up:
+    the checkerboard heat bath on the 16384^2 torus, coalescence times and
+    coupling from the past on 32x32 pairs near the critical curve (the
+    paper's box), and the diagonal sums of a 16384^2 plane."""
+    import numpy as np
+    import torch
+
+    import paper_1908_07341_gb300 as shk
+    from paper_1908_07341_gb300.experiments import critical_J
+    from paper_1908_07341_gb300.lattice import (cftp, checkerboard_run, coalescence_times, diag_correlations)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        s_ev = torch.cuda.Event(enable_timing=True)
+        e_ev = torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e_ev.record(stream)
+        torch.cuda.synchronize()
+        return s_ev.elapsed_time(e_ev) / reps, out
+
+    out = {}
+    Lc = 16384
+    plane = shk.alloc_plane(Lc, "bitpack", device=dev)
+    shk.init_plane("bitpack", plane, Lc, "random", init_seed=INIT_SEED, stream=stream)
+    n_cb = 20
+    ms, _ = timed(lambda: checkerboard_run(plane, Lc, 0.44, SEED, 0, 0, n_cb, obs=True, stream=stream))
+    out["checkerboard"] = {"workload": f"{Lc}x{Lc} square-lattice heat bath, J=0.44, {n_cb} steps with (M, C_nn)",
+                           "value": Lc * Lc * n_cb / (ms / 1e3), "unit": UNIT, "ms": ms,
+                           "gpu_launches": 3 * n_cb}
+    lags = [1, 2, 4, 8, 16]
+    ms, _ = timed(lambda: diag_correlations(plane, Lc, lags, stream=stream), reps=10)
+    out["diag_correlations"] = {"workload": f"{Lc}x{Lc} plane, lags {lags}", "ms": ms,
+                                "value": (Lc * Lc / 8) / (ms / 1e3) / 1e9, "unit": "GB/s of plane read"}
+    del plane
+    n_pairs, L = 1024, 32
+    q = np.repeat(np.array([0.5, 1.0, 1.5, 2.0]), n_pairs // 4)
+    J = critical_J(q) - 0.05
+    ids = np.arange(n_pairs, dtype=np.uint32)
+    max_steps = 1 << 16
+    ms, T = timed(lambda: coalescence_times(np.full(n_pairs, L), q, J, np.uint64(SEED), ids, max_steps,
+                                            device=dev, stream=stream))
+    steps = np.minimum(T.astype(np.float64), max_steps).sum()
+    out["coalescence"] = {"workload": f"{n_pairs} pairs of {L}x{L} tori at J = J_c(q) - 0.05, q in "
+                                      "{0.5, 1, 1.5, 2}", "ms": ms, "pair_steps": steps,
+                          "value": steps * 4 * L * L / (ms / 1e3), "unit": UNIT + " (both chains)"}
+    Jg = critical_J(q) - 0.1
+    ms, (ks, _) = timed(lambda: cftp(np.full(n_pairs, L), q, Jg, np.uint64(SEED), ids, k_max=18,
+                                      device=dev, stream=stream))
+    steps = float(np.sum(2.0 ** (ks[ks >= 0].astype(np.float64) + 1) - 1))
+    out["cftp"] = {"workload": f"{n_pairs} perfect samples of {L}x{L} tori at J = J_c(q) - 0.1",
+                   "ms": ms, "samples_per_s": float((ks >= 0).sum()) / (ms / 1e3),
+                   "value": steps * 4 * L * L / (ms / 1e3), "unit": UNIT + " (both chains, all attempts)"}
+    return out
 
 
 def bench_serving(dev, stream, n_jobs: int = 200, steps_per_launch: int = 2, launches_per_tick: int = 16):
@@ -609,6 +671,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched phase-diagram line")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving line")
+    ap.add_argument("--no-section3", action="store_true", help="skip the Section 3 kernels")
     ap.add_argument("--serving-jobs", type=int, default=200,
                     help="jobs of the serving stream to replay (10000 = the full stream)")
     ap.add_argument("--batch-case", default=None,

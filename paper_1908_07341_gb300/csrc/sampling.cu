@@ -198,6 +198,24 @@ __device__ __forceinline__ void pair_reset(const PairPlanes& p) {
     __syncthreads();
 }
 
+// Draws block w of both coupled chains from one set of uniforms: each Philox
+// call (four planes) serves the two chains, and the lazy loop ends when
+// neither has an undecided site in the warp.  All 32 lanes call it together.
+__device__ __forceinline__ void draw_coupled(const BlockClass (&k)[2], uint32_t w, uint32_t valid, uint32_t hs,
+                                             const DrawParams& P, uint32_t (&up)[2]) {
+    uint32_t und[2] = {valid, valid};
+    up[0] = up[1] = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint4 R = philox_call(w, hs, c, P);
+        apply_planes(R, c, k[0], und[0], up[0], P);
+        apply_planes(R, c, k[1], und[1], up[1], P);
+        if (c < 7 && !__any_sync(0xffffffffu, (und[0] | und[1]) != 0u)) break;
+    }
+    up[0] |= und[0] & k[0].F;
+    up[1] |= und[1] & k[1].F;
+}
+
 // One full step with index t of both chains, driven by the same uniforms
 // (shaken: half-steps A and B; checkerboard: even then odd sites of sigma).
 template <int DYN>
@@ -208,46 +226,42 @@ __device__ __forceinline__ void pair_step(const PairPlanes& p, unsigned long lon
         for (uint32_t base = warp * 32; base < p.nbp; base += nwarps * 32) {
             const uint32_t w = base + lane;
             const bool in = w < p.nb;
+            BlockClass k[2] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
+            uint32_t valid = 0u, S[2] = {0u, 0u};
             if (DYN == kDynShaken) {
-                uint32_t S0 = 0, A0 = 0, B0 = 0, S1 = 0, A1 = 0, B1 = 0;
                 if (in) {
+                    uint32_t A0, B0, A1, B1;
                     if (half == 0) {
-                        smem_fields<0>(p.st, w, p.Wr, p.L, p.nb, S0, A0, B0);
-                        smem_fields<0>(p.sb, w, p.Wr, p.L, p.nb, S1, A1, B1);
+                        smem_fields<0>(p.st, w, p.Wr, p.L, p.nb, S[0], A0, B0);
+                        smem_fields<0>(p.sb, w, p.Wr, p.L, p.nb, S[1], A1, B1);
                     } else {
-                        smem_fields<1>(p.tt, w, p.Wr, p.L, p.nb, S0, A0, B0);
-                        smem_fields<1>(p.tb, w, p.Wr, p.L, p.nb, S1, A1, B1);
+                        smem_fields<1>(p.tt, w, p.Wr, p.L, p.nb, S[0], A0, B0);
+                        smem_fields<1>(p.tb, w, p.Wr, p.L, p.nb, S[1], A1, B1);
                     }
+                    k[0] = block_class(S[0], A0, B0);
+                    k[1] = block_class(S[1], A1, B1);
+                    valid = 0xffffffffu;
                 }
-                const uint32_t S[2] = {S0, S1}, A[2] = {A0, A1}, B[2] = {B0, B1}, ww[2] = {w, w};
-                const uint32_t v[2] = {in ? 0xffffffffu : 0u, in ? 0xffffffffu : 0u};
-                uint32_t up[2];
-                draw_blocks<2>(S, A, B, ww, v, hs + (uint32_t)half, P, up);
-                if (in) {
-                    if (half == 0) {
-                        p.tt[w] = up[0];
-                        p.tb[w] = up[1];
-                    } else {
-                        p.st[w] = up[0];
-                        p.sb[w] = up[1];
-                    }
-                }
-            } else {
+            } else if (in) {
                 // in place: the words read for the neighbour counts keep the
                 // bits of the other parity, which no lane changes now
-                uint32_t* planes2[2] = {p.st, p.sb};
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    uint32_t* pl = planes2[c];
-                    BlockClass k = {0u, 0u, 0u};
-                    uint32_t pm = 0u, S = 0u;
-                    if (in) {
-                        const uint32_t row = w / p.Wr;
-                        k = checkerboard_class(pl, w, row, w - row * p.Wr, p.L, p.Wr, p.nb, (uint32_t)half, pm);
-                        S = pl[w];
-                    }
-                    const uint32_t up = draw_block_class(k, w, pm, hs + (uint32_t)half, P);
-                    if (in) pl[w] = (S & ~pm) | (up & pm);
+                const uint32_t row = w / p.Wr, col = w - row * p.Wr;
+                k[0] = checkerboard_class(p.st, w, row, col, p.L, p.Wr, p.nb, (uint32_t)half, valid);
+                k[1] = checkerboard_class(p.sb, w, row, col, p.L, p.Wr, p.nb, (uint32_t)half, valid);
+                S[0] = p.st[w];
+                S[1] = p.sb[w];
+            }
+            uint32_t up[2];
+            draw_coupled(k, w, valid, hs + (uint32_t)half, P, up);
+            if (in) {
+                if (DYN == kDynShaken) {
+                    uint32_t* d0 = half == 0 ? p.tt : p.st;
+                    uint32_t* d1 = half == 0 ? p.tb : p.sb;
+                    d0[w] = up[0];
+                    d1[w] = up[1];
+                } else {
+                    p.st[w] = (S[0] & ~valid) | (up[0] & valid);
+                    p.sb[w] = (S[1] & ~valid) | (up[1] & valid);
                 }
             }
         }
@@ -349,6 +363,13 @@ cudaError_t launch_diag_corr(const Geometry& g, const void* plane, const int* la
 
 size_t coalesce_smem_bytes(int L) { return 4 * (size_t)(((L * L / 32) + 31) & ~31) * 4; }
 
+// One warp per 32 words of the largest plane, at most 256 threads: a 32 x 32
+// pair runs as a single-warp CTA, so an SM holds many pairs at once.
+static int pair_threads(int max_L) {
+    const int words = (max_L * max_L / 32 + 31) & ~31;
+    return std::min(256, std::max(32, words));
+}
+
 template <class K>
 static cudaError_t allow_smem(K kernel, size_t smem) {
     if (smem > 48 * 1024)
@@ -367,10 +388,10 @@ cudaError_t launch_coalesce(int dyn, const void* pairs, uint32_t n_pairs, int ma
     cudaError_t e;
     if (dyn == kDynShaken) {
         e = allow_smem(k_coalesce<kDynShaken>, smem);
-        if (e == cudaSuccess) k_coalesce<kDynShaken><<<n_pairs, 256, smem, st>>>(a);
+        if (e == cudaSuccess) k_coalesce<kDynShaken><<<n_pairs, pair_threads(max_L), smem, st>>>(a);
     } else {
         e = allow_smem(k_coalesce<kDynCheckerboard>, smem);
-        if (e == cudaSuccess) k_coalesce<kDynCheckerboard><<<n_pairs, 256, smem, st>>>(a);
+        if (e == cudaSuccess) k_coalesce<kDynCheckerboard><<<n_pairs, pair_threads(max_L), smem, st>>>(a);
     }
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
@@ -388,10 +409,10 @@ cudaError_t launch_cftp(int dyn, const void* pairs, uint32_t n_pairs, int max_L,
     cudaError_t e;
     if (dyn == kDynShaken) {
         e = allow_smem(k_cftp<kDynShaken>, smem);
-        if (e == cudaSuccess) k_cftp<kDynShaken><<<n_pairs, 256, smem, st>>>(a);
+        if (e == cudaSuccess) k_cftp<kDynShaken><<<n_pairs, pair_threads(max_L), smem, st>>>(a);
     } else {
         e = allow_smem(k_cftp<kDynCheckerboard>, smem);
-        if (e == cudaSuccess) k_cftp<kDynCheckerboard><<<n_pairs, 256, smem, st>>>(a);
+        if (e == cudaSuccess) k_cftp<kDynCheckerboard><<<n_pairs, pair_threads(max_L), smem, st>>>(a);
     }
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
