@@ -102,6 +102,8 @@ def measure_philox_peak(dev, stream, iters: int = 16384, reps: int = 5) -> float
     """Philox4x32-10 calls per second of the library's own generator with no
     memory traffic (shk_philox_peak: 8 CTAs of 256 threads per SM, independent
     calls per thread), best of `reps` launches timed with events on `stream`."""
+    import torch
+
     from paper_1908_07341_gb300 import _lib
     so = _lib.lib()
     out = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -590,6 +592,24 @@ def run_kernel_case(spec: str) -> int:
 
     parts = spec.split(":")
     layout, side, launches = parts[0], int(parts[1]), int(parts[2])
+    if layout == "checkerboard":             # LAUNCHES / 2 full checkerboard steps at J = 0.44
+        from paper_1908_07341_gb300.lattice import checkerboard_run
+        plane = shk.alloc_plane(side, "bitpack")
+        shk.init_plane("bitpack", plane, side, "random", init_seed=INIT_SEED)
+        rows = checkerboard_run(plane, side, 0.44, SEED, 0, 0, max(1, launches // 2))
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": spec, "last": rows[-1].cpu().tolist()}))
+        return 0
+    if layout == "cftp":                     # LAUNCHES pairs of side x side, one k_cftp launch
+        import numpy as np
+
+        from paper_1908_07341_gb300.experiments import critical_J
+        from paper_1908_07341_gb300.lattice import cftp
+        q = np.full(launches, 1.0)
+        ks, _ = cftp(np.full(launches, side), q, critical_J(q) - 0.1, np.uint64(SEED),
+                     np.arange(launches, dtype=np.uint32), k_max=16)
+        print(json.dumps({"kernel_case": spec, "mean_k": float(ks.mean()), "min_k": int(ks.min())}))
+        return 0
     from paper_1908_07341_gb300 import tune
     if len(parts) > 3:
         tune.set_variant(layout, int(parts[3]))
