@@ -300,9 +300,11 @@ void orc_diag_correlations(const int8_t* s, int L, const int* lags, int n, int64
  * are redrawn given the odd ones, then the odd sites given the even ones,
  * each with P(s_x = +1) = e^{h}/(2 cosh h), h = J (sum of the four
  * neighbours) (heat bath).  Thresholds by the rule of reading R4, indexed by
- * the number n = 0..4 of + neighbours, h = J (2n - 4).  The uniform of site u
- * in half-step hs is the block uniform of reading R5 with counter
- * (hs, u >> 5, lattice_id, 512 + c). */
+ * the number n = 0..4 of + neighbours, h = J (2n - 4).  The uniforms are
+ * spent only on the sites being redrawn: those sites, numbered row by row,
+ * a = j (L/2) + floor(i/2) (each row holds one of every pair of columns
+ * (2m, 2m+1)), take the block uniforms of reading R5 with counter
+ * (hs, a >> 5, lattice_id, 512 + c), column a & 31. */
 int orc_checkerboard_thresholds(double J, uint32_t T[5]) {
     if (!isfinite(J)) return -1;
     for (int n = 0; n < 5; ++n) T[n] = orc_threshold_of(J * (double)(2 * n - 4));
@@ -319,12 +321,13 @@ void orc_checkerboard_halfstep(int8_t* s, int L, const uint32_t T[5], uint64_t s
             int64_t u = j * L + i;
             int n = (s[orc_wrap(j + 1, L) * L + i] > 0) + (s[orc_wrap(j - 1, L) * L + i] > 0) +
                     (s[j * L + orc_wrap(i + 1, L)] > 0) + (s[j * L + orc_wrap(i - 1, L)] > 0);
-            int64_t w = u >> 5;
+            int64_t a = j * (L / 2) + i / 2;   /* index among the redrawn sites */
+            int64_t w = a >> 5;
             if (w != cached_w) {
                 orc_block_uniforms(seed, hs, (uint32_t)w, lattice_id, 2u, r);
                 cached_w = w;
             }
-            s[u] = (r[u & 31] < T[n]) ? 1 : -1;
+            s[u] = (r[a & 31] < T[n]) ? 1 : -1;
         }
     }
 }

@@ -3,8 +3,8 @@
 //   k_diag_corr          SW-NE / NW-SE spin-spin sums at up to eight lags
 //                        (Section 3.3, Table 1)
 //   k_checkerboard<P>    the square-lattice heat bath on the sites of one
-//                        parity (the comparison dynamics of Section 3.2)
-//   k_sq_obs             magnetisation and C_nn of a plane
+//                        parity (the comparison dynamics of Section 3.2), with
+//                        the magnetisation and C_nn fused into the odd half
 //   k_coalesce<DYN>      coalescence times of the all + / all - coupling
 //   k_cftp<DYN>          Propp-Wilson coupling from the past
 // The draw machinery (Philox, lazy bit-serial comparison) is the half-steps'
@@ -85,54 +85,220 @@ __global__ void __launch_bounds__(256) k_diag_corr(const CorrArgs a) {
 }
 
 // ------------------------------------------------------------ checkerboard heat bath
-
+//
 // The square-lattice comparison dynamics of Section 3.2: the sites with
 // (i + j) % 2 == parity are redrawn in place, P(+1) = e^h / (2 cosh h) with
 // h = J (2n - 4), n the number of + among the four neighbours (all of the
-// other parity, so unchanged while the parity is redrawn).  With the
-// complement rule the five thresholds fold onto the three-class draw: sites
-// with n < 2 compare their complemented uniform, and the class is
-// n' = max(n, 4 - n) - 2 with thresholds (T[2], T[3], T[4]).  Returns the
-// classes of block w (row, col) of a bit-packed plane and sets pm to the mask
-// of its sites of the given parity.
-__device__ __forceinline__ BlockClass checkerboard_class(const uint32_t* pl, uint32_t w, uint32_t row,
-                                                         uint32_t col, uint32_t L, uint32_t Wr,
-                                                         uint32_t nblocks, uint32_t parity, uint32_t& pm) {
+// other parity, so unchanged while the parity is redrawn).
+//
+// Only the redrawn sites consume uniforms: numbered row by row,
+// a = j (L/2) + floor(i/2), they fill draw blocks of 32, and draw block d
+// (uniforms of counter word d) covers exactly the active sites of plane words
+// 2d and 2d + 1 (16 each, in order).  A thread gathers those 32 sites and
+// their neighbours into 32-bit words by bit compaction, draws them with the
+// half-steps' machinery, and spreads the result back.
+//
+// With the complement rule the five thresholds fold onto the three-class
+// draw: sites with n < 2 compare their complemented uniform, and the class
+// is max(n, 4 - n) - 2 with thresholds (T[2], T[3], T[4]).
+
+// The 16 bits of x at even positions 0, 2, .., 30, compacted to bits 0..15.
+__device__ __forceinline__ uint32_t even_bits(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+
+// Inverse of even_bits: bits 0..15 of x to positions 0, 2, .., 30.
+__device__ __forceinline__ uint32_t spread_even(uint32_t x) {
+    x &= 0x0000FFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// The four neighbour bits (up, down, left, right) of the 16 active sites of
+// plane word w, compacted, and the word's active offset o (active sites at
+// bit positions o, o + 2, ..).
+struct CbWord {
+    uint32_t U, D, Lf, Rt, o;
+};
+
+__device__ __forceinline__ CbWord cb_word(const uint32_t* pl, uint32_t w, uint32_t row, uint32_t col, uint32_t L,
+                                          uint32_t Wr, uint32_t nblocks, uint32_t parity) {
+    CbWord r;
+    r.o = (row + parity) & 1u;
     const uint32_t S = pl[w];
     const uint32_t U = pl[row + 1 < L ? w + Wr : w + Wr - nblocks];
     const uint32_t D = pl[row > 0 ? w - Wr : w + nblocks - Wr];
-    const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
-    const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
-    const uint32_t Lf = (S << 1) | (prev >> 31);
-    const uint32_t Rt = (S >> 1) | (next << 31);
+    r.U = even_bits(U >> r.o);
+    r.D = even_bits(D >> r.o);
+    if (r.o == 0) {   // active at even positions: left and right neighbours are the odd bits
+        const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
+        const uint32_t odd = even_bits(S >> 1);
+        r.Rt = odd;
+        r.Lf = ((odd << 1) | (prev >> 31)) & 0xFFFFu;
+    } else {          // active at odd positions: neighbours are the even bits
+        const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
+        const uint32_t even = even_bits(S);
+        r.Lf = even;
+        r.Rt = (even >> 1) | ((next & 1u) << 15);
+    }
+    return r;
+}
+
+// Class masks of draw block d (plane words 2d and 2d + 1) and the compacted
+// neighbour words (for the fused C_nn).
+struct CbBlock {
+    BlockClass k;
+    uint32_t U, D, Lf, Rt;
+    uint32_t o0, o1;
+};
+
+__device__ __forceinline__ CbBlock cb_block(const uint32_t* pl, uint32_t d, uint32_t r0, uint32_t r1, uint32_t L,
+                                            uint32_t Wr, uint32_t nblocks, uint32_t parity) {
+    const uint32_t w0 = 2 * d, w1 = w0 + 1;
+    const CbWord a = cb_word(pl, w0, r0, w0 - r0 * Wr, L, Wr, nblocks, parity);
+    const CbWord b = cb_word(pl, w1, r1, w1 - r1 * Wr, L, Wr, nblocks, parity);
+    CbBlock c;
+    c.U = a.U | (b.U << 16);
+    c.D = a.D | (b.D << 16);
+    c.Lf = a.Lf | (b.Lf << 16);
+    c.Rt = a.Rt | (b.Rt << 16);
+    c.o0 = a.o;
+    c.o1 = b.o;
     // n = U + D + Lf + Rt per site, as bits b0 + 2 b1 + 4 b2
-    const uint32_t ab_s = U ^ D, ab_c = U & D, cd_s = Lf ^ Rt, cd_c = Lf & Rt;
+    const uint32_t ab_s = c.U ^ c.D, ab_c = c.U & c.D, cd_s = c.Lf ^ c.Rt, cd_c = c.Lf & c.Rt;
     const uint32_t b0 = ab_s ^ cd_s, c0 = ab_s & cd_s;
     const uint32_t b1 = ab_c ^ cd_c ^ c0;
     const uint32_t b2 = (ab_c & cd_c) | ((ab_c ^ cd_c) & c0);
     const uint32_t extreme = b2 | ~(b0 | b1 | b2);       // n == 4 or n == 0
-    pm = ((row & 1u) == parity) ? 0x55555555u : 0xAAAAAAAAu;
-    BlockClass k;
-    k.F = ~(b1 | b2);                                   // n < 2
-    k.C2 = extreme;
-    k.Cg = b0 | extreme;                                // n odd or extreme
-    return k;
+    c.k.F = ~(b1 | b2);                                 // n < 2
+    c.k.C2 = extreme;
+    c.k.Cg = b0 | extreme;                              // n odd or extreme
+    return c;
+}
+
+// Writes the 32 drawn spins of draw block d back into plane words 2d, 2d + 1
+// (their other bits are unchanged); returns the new words.
+__device__ __forceinline__ uint2 cb_store(uint32_t* pl, uint32_t d, uint32_t up, uint32_t o0, uint32_t o1) {
+    const uint32_t w0 = 2 * d;
+    const uint32_t m0 = 0x55555555u << o0, m1 = 0x55555555u << o1;
+    const uint32_t v0 = (pl[w0] & ~m0) | (spread_even(up) << o0);
+    const uint32_t v1 = (pl[w0 + 1] & ~m1) | (spread_even(up >> 16) << o1);
+    pl[w0] = v0;
+    pl[w0 + 1] = v1;
+    return make_uint2(v0, v1);
+}
+
+// Adds the fused sums of a finished draw block: the magnetisation of its two
+// words and, for the odd half (every bond has exactly one odd end), the bonds
+// of its 32 redrawn sites.
+__device__ __forceinline__ void cb_accumulate(int (&acc)[2], uint2 v, uint32_t up, uint32_t U, uint32_t D,
+                                              uint32_t Lf, uint32_t Rt) {
+    acc[0] += 2 * (__popc(v.x) + __popc(v.y)) - 64;
+    acc[1] += 128 - 2 * (__popc(up ^ U) + __popc(up ^ D) + __popc(up ^ Lf) + __popc(up ^ Rt));
+}
+
+// Queue fields of a parked draw block: d, und, up, F, Cg, C2 (the neighbour
+// words for the sums are gathered again when it is finished).
+template <int PARITY>
+__device__ __forceinline__ void cb_finish(const SweepArgs& a, uint32_t* pl, uint32_t d, uint32_t up, uint32_t o0,
+                                          uint32_t o1, int (&acc)[2], const CbBlock* known) {
+    const uint2 v = cb_store(pl, d, up, o0, o1);
+    if (PARITY == 1 && a.obs_cur != nullptr) {
+        if (known != nullptr) {
+            cb_accumulate(acc, v, up, known->U, known->D, known->Lf, known->Rt);
+        } else {
+            const CbBlock c = cb_block(pl, d, fdiv(2 * d, a.div_row), fdiv(2 * d + 1, a.div_row), a.L, a.Wr,
+                                       a.nblocks, PARITY);
+            cb_accumulate(acc, v, up, c.U, c.D, c.Lf, c.Rt);
+        }
+    }
+}
+
+// Continues the `take` (<= 32) oldest parked draw blocks from Philox call 2;
+// all lanes call it.
+template <int PARITY>
+__device__ __forceinline__ void cb_drain(const SweepArgs& a, uint32_t* pl, uint32_t (*q)[kQueueCap], uint32_t head,
+                                         int take, int (&acc)[2]) {
+    const uint32_t lane = threadIdx.x & 31;
+    const bool has = (int)lane < take;
+    const uint32_t i = (head + lane) & (kQueueCap - 1);
+    BlockClass k = {0u, 0u, 0u};
+    uint32_t d = 0, und = 0, up = 0;
+    if (has) {
+        d = q[0][i];
+        und = q[1][i];
+        up = q[2][i];
+        k.F = q[3][i];
+        k.Cg = q[4][i];
+        k.C2 = q[5][i];
+    }
+    const uint32_t res = draw_rest(k, d, und, up, a.hs, a.P);
+    if (has) {
+        const uint32_t r0 = fdiv(2 * d, a.div_row), r1 = fdiv(2 * d + 1, a.div_row);
+        cb_finish<PARITY>(a, pl, d, res, (r0 + PARITY) & 1u, (r1 + PARITY) & 1u, acc, nullptr);
+    }
 }
 
 template <int PARITY>
-__global__ void __launch_bounds__(256) k_checkerboard(const SweepArgs a) {
+__global__ void __launch_bounds__(256, 3) k_checkerboard(const SweepArgs a) {
+    __shared__ uint32_t qbuf[8][6][kQueueCap];
     uint32_t* pl = static_cast<uint32_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
-        const uint32_t w = base + lane;
-        const uint32_t row = fdiv(w, a.div_row);
-        uint32_t pm;
-        const BlockClass k = checkerboard_class(pl, w, row, w - row * a.Wr, a.L, a.Wr, a.nblocks, PARITY, pm);
-        const uint32_t S = pl[w];
-        const uint32_t up = draw_block_class(k, w, pm, a.hs, a.P);
-        pl[w] = (S & ~pm) | (up & pm);
+    const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
+    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    const uint32_t nd = a.nblocks / 2;
+    const uint32_t below = (1u << lane) - 1u;
+    int acc[2] = {0, 0};
+    uint32_t head = 0;
+    int count = 0;
+    for (uint32_t base = gwarp * 32; base < nd; base += stride) {
+        const uint32_t d = base + lane;
+        const bool in = d < nd;
+        CbBlock c;
+        c.k = {0u, 0u, 0u};
+        c.o0 = c.o1 = 0u;
+        if (in) c = cb_block(pl, d, fdiv(2 * d, a.div_row), fdiv(2 * d + 1, a.div_row), a.L, a.Wr, a.nblocks, PARITY);
+        uint32_t und, up;
+        draw_first_two(c.k, d, in ? 0xffffffffu : 0u, a.hs, a.P, und, up);
+        const bool parked = und != 0u;
+        const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+        if (parked) {
+            const uint32_t i = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+            q[0][i] = d;
+            q[1][i] = und;
+            q[2][i] = up;
+            q[3][i] = c.k.F;
+            q[4][i] = c.k.Cg;
+            q[5][i] = c.k.C2;
+        } else if (in) {
+            cb_finish<PARITY>(a, pl, d, up, c.o0, c.o1, acc, &c);
+        }
+        count += __popc(mask);
+        if (count >= 32) {
+            __syncwarp();
+            cb_drain<PARITY>(a, pl, q, head, 32, acc);
+            __syncwarp();
+            head = (head + 32) & (kQueueCap - 1);
+            count -= 32;
+        }
+    }
+    if (count > 0) {
+        __syncwarp();
+        cb_drain<PARITY>(a, pl, q, head, count, acc);
+    }
+    if (PARITY == 1) {
+        const int v[2] = {acc[0], acc[1]};
+        long long* const dst[2] = {a.obs_cur, a.obs_cur ? a.obs_cur + 1 : nullptr};
+        block_accumulate<2>(v, dst);
     }
 }
 
@@ -217,51 +383,60 @@ __device__ __forceinline__ void draw_coupled(const BlockClass (&k)[2], uint32_t 
 }
 
 // One full step with index t of both chains, driven by the same uniforms
-// (shaken: half-steps A and B; checkerboard: even then odd sites of sigma).
+// (shaken: half-steps A and B over the plane words; checkerboard: even then
+// odd sites of sigma over the draw blocks of two words each).
 template <int DYN>
 __device__ __forceinline__ void pair_step(const PairPlanes& p, unsigned long long t, const DrawParams& P) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t hs = (uint32_t)(2 * t);
     for (int half = 0; half < 2; ++half) {
-        for (uint32_t base = warp * 32; base < p.nbp; base += nwarps * 32) {
-            const uint32_t w = base + lane;
-            const bool in = w < p.nb;
-            BlockClass k[2] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
-            uint32_t valid = 0u, S[2] = {0u, 0u};
-            if (DYN == kDynShaken) {
+        if (DYN == kDynShaken) {
+            for (uint32_t base = warp * 32; base < p.nbp; base += nwarps * 32) {
+                const uint32_t w = base + lane;
+                const bool in = w < p.nb;
+                BlockClass k[2] = {{0u, 0u, 0u}, {0u, 0u, 0u}};
                 if (in) {
-                    uint32_t A0, B0, A1, B1;
+                    uint32_t S0, A0, B0, S1, A1, B1;
                     if (half == 0) {
-                        smem_fields<0>(p.st, w, p.Wr, p.L, p.nb, S[0], A0, B0);
-                        smem_fields<0>(p.sb, w, p.Wr, p.L, p.nb, S[1], A1, B1);
+                        smem_fields<0>(p.st, w, p.Wr, p.L, p.nb, S0, A0, B0);
+                        smem_fields<0>(p.sb, w, p.Wr, p.L, p.nb, S1, A1, B1);
                     } else {
-                        smem_fields<1>(p.tt, w, p.Wr, p.L, p.nb, S[0], A0, B0);
-                        smem_fields<1>(p.tb, w, p.Wr, p.L, p.nb, S[1], A1, B1);
+                        smem_fields<1>(p.tt, w, p.Wr, p.L, p.nb, S0, A0, B0);
+                        smem_fields<1>(p.tb, w, p.Wr, p.L, p.nb, S1, A1, B1);
                     }
-                    k[0] = block_class(S[0], A0, B0);
-                    k[1] = block_class(S[1], A1, B1);
-                    valid = 0xffffffffu;
+                    k[0] = block_class(S0, A0, B0);
+                    k[1] = block_class(S1, A1, B1);
                 }
-            } else if (in) {
-                // in place: the words read for the neighbour counts keep the
-                // bits of the other parity, which no lane changes now
-                const uint32_t row = w / p.Wr, col = w - row * p.Wr;
-                k[0] = checkerboard_class(p.st, w, row, col, p.L, p.Wr, p.nb, (uint32_t)half, valid);
-                k[1] = checkerboard_class(p.sb, w, row, col, p.L, p.Wr, p.nb, (uint32_t)half, valid);
-                S[0] = p.st[w];
-                S[1] = p.sb[w];
-            }
-            uint32_t up[2];
-            draw_coupled(k, w, valid, hs + (uint32_t)half, P, up);
-            if (in) {
-                if (DYN == kDynShaken) {
+                uint32_t up[2];
+                draw_coupled(k, w, in ? 0xffffffffu : 0u, hs + (uint32_t)half, P, up);
+                if (in) {
                     uint32_t* d0 = half == 0 ? p.tt : p.st;
                     uint32_t* d1 = half == 0 ? p.tb : p.sb;
                     d0[w] = up[0];
                     d1[w] = up[1];
-                } else {
-                    p.st[w] = (S[0] & ~valid) | (up[0] & valid);
-                    p.sb[w] = (S[1] & ~valid) | (up[1] & valid);
+                }
+            }
+        } else {
+            // in place: the words read for the neighbours keep the bits of the
+            // other parity, which no lane changes now
+            const uint32_t nd = p.nb / 2;
+            for (uint32_t base = warp * 32; base < nd; base += nwarps * 32) {
+                const uint32_t d = base + lane;
+                const bool in = d < nd;
+                CbBlock c0, c1;
+                c0.k = c1.k = {0u, 0u, 0u};
+                c0.o0 = c0.o1 = 0u;
+                if (in) {
+                    const uint32_t r0 = (2 * d) / p.Wr, r1 = (2 * d + 1) / p.Wr;
+                    c0 = cb_block(p.st, d, r0, r1, p.L, p.Wr, p.nb, (uint32_t)half);
+                    c1 = cb_block(p.sb, d, r0, r1, p.L, p.Wr, p.nb, (uint32_t)half);
+                }
+                const BlockClass k[2] = {c0.k, c1.k};
+                uint32_t up[2];
+                draw_coupled(k, d, in ? 0xffffffffu : 0u, hs + (uint32_t)half, P, up);
+                if (in) {
+                    cb_store(p.st, d, up[0], c0.o0, c0.o1);
+                    cb_store(p.sb, d, up[1], c0.o0, c0.o1);
                 }
             }
         }
@@ -324,24 +499,6 @@ __global__ void __launch_bounds__(256) k_cftp(const CftpArgs a) {
     for (uint32_t w = threadIdx.x; w < a.sample_words; w += blockDim.x)
         out[w] = (result >= 0 && w < p.nb) ? p.st[w] : 0u;
     if (threadIdx.x == 0) a.k_out[pi] = result;
-}
-
-// Magnetisation and C_nn = sum_x s_x (s_{x down} + s_{x left}) (equal by
-// translation to the up/right form) of a bit-packed plane, added to out[0..1].
-__global__ void __launch_bounds__(256) k_sq_obs(const SweepArgs a) {
-    int m = 0, c = 0;
-    const uint32_t* pl = static_cast<const uint32_t*>(a.src);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
-        const uint32_t row = fdiv(w, a.div_row);
-        uint32_t S, N1, N2;
-        words_aligned<0>(pl, w, row, w - row * a.Wr, a.L, a.Wr, a.nblocks, S, N1, N2);
-        m += 2 * __popc(S) - 32;
-        c += 64 - 2 * (__popc(S ^ N1) + __popc(S ^ N2));
-    }
-    const int v[2] = {m, c};
-    long long* const d[2] = {a.obs_cur, a.obs_cur ? a.obs_cur + 1 : nullptr};
-    block_accumulate<2>(v, d);
 }
 
 // ------------------------------------------------------------ host side
@@ -432,15 +589,13 @@ cudaError_t launch_checkerboard(const Geometry& g, void* plane, const DrawParams
                                 long long* obs, cudaStream_t st) {
     SweepArgs a = sweep_args(g, plane, plane, P, hs, obs, nullptr, nullptr);
     const int block = 256;
+    const uint64_t draw_blocks = g.nblocks / 2;   // 32 redrawn sites each
     if (parity == 0) {
-        k_checkerboard<0><<<grid_for(k_checkerboard<0>, block, g.nblocks), block, 0, st>>>(a);
+        k_checkerboard<0><<<grid_for(k_checkerboard<0>, block, draw_blocks), block, 0, st>>>(a);
     } else {
-        k_checkerboard<1><<<grid_for(k_checkerboard<1>, block, g.nblocks), block, 0, st>>>(a);
+        k_checkerboard<1><<<grid_for(k_checkerboard<1>, block, draw_blocks), block, 0, st>>>(a);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && obs != nullptr && parity == 1)
-        k_sq_obs<<<grid_for(k_sq_obs, block, g.nblocks), block, 0, st>>>(a);
-    return e == cudaSuccess ? cudaGetLastError() : e;
+    return cudaGetLastError();
 }
 
 }  // namespace shk
