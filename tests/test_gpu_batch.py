@@ -101,26 +101,26 @@ def test_batch_argument_errors():
         Batch(L=[33], q=[1.0], J=[0.3], seed=[1], lattice_id=[0])
 
 
-def test_full_phase_diagram_batch_one_step_spot_checks(orc):
+def test_full_phase_diagram_batch_spot_checks(orc):
     """The whole 1024-lattice phase-diagram batch in a launch shape of the
     kind the benchmark uses (8 steps per launch, 256 threads, 2^18-site
-    tiles): after 99 steps, the oracle takes the GPU's sigma of sampled
-    lattices (the largest and smallest included) and runs step 99 itself;
-    sigma and tau after step 100 must agree bit for bit."""
+    tiles): after 96 steps, the oracle takes the GPU's sigma of sampled
+    lattices (the largest and smallest included) and runs steps 96..103
+    itself; sigma and tau after the GPU's next launch must agree bit for bit."""
     w = workloads.phase_diagram_batch()
     b = Batch(w["L"], w["q"], w["J"], w["seed"], w["lattice_id"]).configure(8, 256, 1 << 18)
     b.init("random", init_seed=w["init_seed"])
-    b.run(99)
+    b.run(96)
     rng = np.random.default_rng(0)
     sample = sorted(set(rng.choice(len(w["L"]), size=10, replace=False).tolist()
                         + [int(np.argmax(w["L"])), int(np.argmin(w["L"]))]))
     before = {i: b.read_spins(i, 0).reshape(-1).astype(np.int8) for i in sample}
-    b.run(1)
+    b.run(8)
     for i in sample:
         L = int(w["L"][i])
         sigma = before[i].copy()
         tau = np.zeros(L * L, np.int8)
         orc.run(sigma, tau, L, float(w["q"][i]), float(w["J"][i]), int(w["seed"][i]), int(w["lattice_id"][i]),
-                99, 1, want_obs=False)
+                96, 8, want_obs=False)
         assert np.array_equal(b.read_spins(i, 0).reshape(-1), sigma), i
         assert np.array_equal(b.read_spins(i, 1).reshape(-1), tau), i
