@@ -177,11 +177,14 @@ int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags,
  * step t redraws the sites with i + j even (half-step index 2t), then those
  * with i + j odd (2t + 1), each +1 with probability e^h / (2 cosh h),
  * h = J (2n - 4), n the number of + among its four neighbours.  Thresholds
- * T[n] by the rule of shk_thresholds; the uniform of site u in half-step hs is
- * the block construction of this header with counter (hs, u >> 5, lattice_id,
- * 512 + c).  plane: device bit-packed sigma (L % 32 == 0), updated in place;
- * dev_obs (nullable): n_steps rows of (M, C_nn) int64, H_G = -J C_nn.
- * Asynchronous. */
+ * T[n] by the rule of shk_thresholds.  Only the redrawn sites consume
+ * uniforms: numbered row by row, a = j (L/2) + floor(i/2), site a takes column
+ * a & 31 of the block construction of this header with counter
+ * (hs, a >> 5, lattice_id, 512 + c).  plane: device bit-packed sigma
+ * (L % 32 == 0), updated in place; dev_obs (nullable): n_steps rows of
+ * (M, C_nn) int64, C_nn = sum_x s_x (s_{x up} + s_{x right}), H_G = -J C_nn.
+ * Errors: SHK_EINVAL for a bad L, a NULL plane, a non-finite J or steps past
+ * 2^31.  Asynchronous. */
 int shk_checkerboard_thresholds(double J, uint32_t out[5]);
 int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
                          uint64_t n_steps, int64_t* dev_obs, void* stream);
