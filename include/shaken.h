@@ -344,7 +344,11 @@ int shk_batch_read_spins(shk_batch* b, int idx, int plane, int8_t* host_out);
 
 /* A simulation request: one bit-packed lattice pair of side L (32 <= L <=
  * 8192, L % 32 == 0) run for n_steps full steps from an initial state, with
- * the statistics of the steps t >= burn_in (as in shk_batch). */
+ * the statistics of the steps t >= burn_in (as in shk_batch).  deadline_ticks
+ * (0 = none): a job not finished within that many scheduler ticks of its
+ * submission is retired with status SHK_ETIMEOUT at the end of the tick that
+ * reaches the deadline, queued or running; a running one reports the steps it
+ * completed, their statistics and the hash of its sigma at that point. */
 typedef struct {
     int L;
     double q, J;
@@ -354,13 +358,15 @@ typedef struct {
     uint64_t init_seed;
     uint64_t n_steps;
     uint64_t burn_in;
+    uint64_t deadline_ticks;
 } shk_job;
 
-/* A finished (or cancelled) job.  sigma_hash is the 64-bit FNV-1a hash of the
- * final sigma plane's bytes (bit-packed layout); ticks count scheduler ticks. */
+/* A finished, cancelled or expired job.  sigma_hash is the 64-bit FNV-1a hash
+ * of the final sigma plane's bytes (bit-packed layout; 0 for a job that never
+ * ran or was cancelled); ticks count scheduler ticks. */
 typedef struct {
     uint64_t job_id;
-    int status;             /* SHK_OK or SHK_ECANCELLED */
+    int status;             /* SHK_OK, SHK_ECANCELLED or SHK_ETIMEOUT */
     uint64_t steps_done;
     int64_t stats[SHK_NSTATS];
     int64_t last_obs[SHK_NOBS];
@@ -393,6 +399,9 @@ int shk_server_configure(shk_server* s, int steps_per_launch, int launches_per_t
                          int tile_sites, size_t max_pending);
 int shk_server_submit(shk_server* s, const shk_job* job, uint64_t* job_id);
 int shk_server_cancel(shk_server* s, uint64_t job_id);
+/* One scheduler tick: admission, the tick's launches, retirement of finished
+ * jobs, then expiry of jobs whose deadline tick has been reached.  Every call
+ * advances the tick counter by one, with or without work. */
 int shk_server_tick(shk_server* s, int* n_active, int* n_pending);
 int shk_server_poll(shk_server* s, shk_result* out, int max, int* n_out);
 int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes);

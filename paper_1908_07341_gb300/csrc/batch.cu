@@ -1121,6 +1121,28 @@ int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
         s->tick += 1;
         for (int i = 0; i < s->max_slots; ++i)
             if (s->slots[i].used && s->slots[i].remaining == 0) retire(s, i, SHK_OK, true);
+    } else {
+        s->tick += 1;
+    }
+    // (4) deadlines: unfinished jobs whose deadline tick has been reached
+    for (int i = 0; i < s->max_slots; ++i) {
+        const Slot& sl = s->slots[i];
+        if (sl.used && sl.job.deadline_ticks && s->tick >= sl.submit_tick + sl.job.deadline_ticks)
+            retire(s, i, SHK_ETIMEOUT, true);
+    }
+    for (auto it = s->pending.begin(); it != s->pending.end();) {
+        if (it->job.deadline_ticks && s->tick >= it->submit_tick + it->job.deadline_ticks) {
+            shk_result r;
+            std::memset(&r, 0, sizeof r);
+            r.job_id = it->job_id;
+            r.status = SHK_ETIMEOUT;
+            r.submit_tick = it->submit_tick;
+            r.done_tick = s->tick;
+            s->done.push_back(r);
+            it = s->pending.erase(it);
+        } else {
+            ++it;
+        }
     }
     int active = 0;
     for (const Slot& sl : s->slots) active += sl.used ? 1 : 0;

@@ -22,7 +22,8 @@ _INITS = {"up": _lib.INIT_ALL_UP, "down": _lib.INIT_ALL_DOWN, "random": _lib.INI
 class Job(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("q", ctypes.c_double), ("J", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("lattice_id", ctypes.c_uint32), ("init_kind", ctypes.c_int),
-                ("init_seed", ctypes.c_uint64), ("n_steps", ctypes.c_uint64), ("burn_in", ctypes.c_uint64)]
+                ("init_seed", ctypes.c_uint64), ("n_steps", ctypes.c_uint64), ("burn_in", ctypes.c_uint64),
+                ("deadline_ticks", ctypes.c_uint64)]
 
 
 class Result(ctypes.Structure):
@@ -79,9 +80,12 @@ class Server:
                                           int(block_threads), int(tile_sites), int(max_pending)), self._h)
         return self
 
-    def submit(self, L, q, J, seed, lattice_id, n_steps, burn_in=0, init="random", init_seed=0) -> int:
+    def submit(self, L, q, J, seed, lattice_id, n_steps, burn_in=0, init="random", init_seed=0,
+               deadline_ticks=0) -> int:
+        """Queues a job; deadline_ticks > 0 retires it with SHK_ETIMEOUT if it
+        is not finished within that many ticks of its submission."""
         job = Job(int(L), float(q), float(J), int(seed) & (2 ** 64 - 1), int(lattice_id),
-                  _INITS.get(init, init), int(init_seed), int(n_steps), int(burn_in))
+                  _INITS.get(init, init), int(init_seed), int(n_steps), int(burn_in), int(deadline_ticks))
         jid = ctypes.c_uint64()
         _check(lib().shk_server_submit(self._h, ctypes.byref(job), ctypes.byref(jid)), self._h)
         return int(jid.value)

@@ -112,3 +112,32 @@ def test_queue_limit_cancel_and_validation():
     with pytest.raises(shk.ShakenError):
         srv.cancel(12345)
     assert srv.tick() == (0, 0)
+
+
+def test_deadlines_expire_queued_and_running_jobs():
+    """One slot, 4 steps per tick.  Job a (deadline 3 ticks) is still running
+    at the end of tick 3 and is retired with SHK_ETIMEOUT after 12 steps, its
+    statistics and sigma hash those of the first 12 steps of a single-lattice
+    run; job b (deadline 2) expires in the queue without running; job c (no
+    deadline) then runs to completion unaffected."""
+    srv = Server(max_slots=1, arena_bytes=8 << 20).configure(steps_per_launch=2, launches_per_tick=2)
+    ja = dict(L=64, q=1.0, J=0.3, seed=1, lattice_id=0, n_steps=40, burn_in=4, init_seed=7)
+    jb = dict(L=64, q=0.5, J=0.4, seed=2, lattice_id=1, n_steps=8, burn_in=0, init_seed=7)
+    jc = dict(L=32, q=2.0, J=0.44, seed=3, lattice_id=2, n_steps=8, burn_in=0, init_seed=7)
+    a = srv.submit(**ja, deadline_ticks=3)
+    b = srv.submit(**jb, deadline_ticks=2)
+    c = srv.submit(**jc)
+    got = {}
+    for _ in range(20):
+        srv.tick()
+        got.update({r["job_id"]: r for r in srv.poll()})
+        if len(got) == 3:
+            break
+    assert got[a]["status"] == -6 and got[a]["steps_done"] == 12 and got[a]["done_tick"] == 3
+    stats, last, h = _single(dict(ja, n_steps=12))
+    assert np.array_equal(got[a]["stats"], stats) and np.array_equal(got[a]["last_obs"], last)
+    assert got[a]["sigma_hash"] == h
+    assert got[b]["status"] == -6 and got[b]["steps_done"] == 0 and got[b]["done_tick"] == 2
+    assert got[c]["status"] == 0 and got[c]["steps_done"] == 8 and got[c]["admit_tick"] == 3
+    stats, last, h = _single(jc)
+    assert np.array_equal(got[c]["stats"], stats) and got[c]["sigma_hash"] == h
