@@ -165,6 +165,44 @@ __device__ __forceinline__ uint4 philox_call(uint32_t w, uint32_t hs, int c, con
     return make_uint4(x0, x1, x2, x3);
 }
 
+// The warp-uniform part of the first three Philox rounds of one call.  In a
+// half-step the counter (hs, w, lattice_id, c3) varies across threads only in
+// the block index w, and w enters round 1 only through an XOR.  Folding the
+// uniform words into constants leaves one varying product in round 2, one in
+// round 3 and two in each of rounds 4 to 10 (round function as in philox10):
+//   after round 1: c = (A ^ w, u1, u2, u3)            (u1..u3 uniform)
+//   after round 2: c = (u4, u5, hi(M0 x1) ^ K2, lo(M0 x1)),  x1 = A ^ w
+//   after round 3: c = (hi(M1 x2) ^ K3, lo(M1 x2), H3 ^ lo(M0 x1), D),
+//                  x2 = hi(M0 x1) ^ K2
+// The host computes (A, K2, K3, H3, D) per call and half-step.
+struct PhiloxPrefix {
+    uint32_t A, K2, K3, H3, D;
+};
+
+template <class PP>
+__device__ __forceinline__ uint4 philox_call_pre(uint32_t w, const PhiloxPrefix& u, const PP& P) {
+    const uint32_t x1 = u.A ^ w;
+    const uint32_t x2 = __umulhi(kPhiloxM0, x1) ^ u.K2;
+    uint32_t c0 = __umulhi(kPhiloxM1, x2) ^ u.K3;
+    uint32_t c1 = kPhiloxM1 * x2;
+    uint32_t c2 = u.H3 ^ (kPhiloxM0 * x1);
+    uint32_t c3 = u.D;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        const uint32_t lo0 = kPhiloxM0 * c0;
+        const uint32_t hi0 = __umulhi(kPhiloxM0, c0);
+        const uint32_t lo1 = kPhiloxM1 * c2;
+        const uint32_t hi1 = __umulhi(kPhiloxM1, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ P.rk0[r];
+        const uint32_t n2 = hi0 ^ c3 ^ P.rk1[r];
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 // Applies the four planes of call c to the state (und, up) of one block.
 template <class PP>
 __device__ __forceinline__ void apply_planes(const uint4& R, int c, const BlockClass& k, uint32_t& und,
@@ -190,6 +228,33 @@ __device__ __forceinline__ void draw_first_two(const BlockClass& k, uint32_t w, 
     up = 0;
     apply_planes(R0, 0, k, und, up, P);
     apply_planes(R1, 1, k, und, up, P);
+}
+
+// Phase 1 with the host-computed round prefixes of the half-step (pre[c] for
+// call c); the same draw as draw_first_two.
+template <class PP>
+__device__ __forceinline__ void draw_first_two_pre(const BlockClass& k, uint32_t w, uint32_t valid,
+                                                   const PhiloxPrefix (&pre)[8], const PP& P, uint32_t& und,
+                                                   uint32_t& up) {
+    const uint4 R0 = philox_call_pre(w, pre[0], P);
+    const uint4 R1 = philox_call_pre(w, pre[1], P);
+    und = valid;
+    up = 0;
+    apply_planes(R0, 0, k, und, up, P);
+    apply_planes(R1, 1, k, und, up, P);
+}
+
+// Phase 2 with the round prefixes; the same draw as draw_rest.
+template <class PP>
+__device__ __forceinline__ uint32_t draw_rest_pre(const BlockClass& k, uint32_t w, uint32_t und, uint32_t up,
+                                                  const PhiloxPrefix (&pre)[8], const PP& P) {
+#pragma unroll
+    for (int c = 2; c < 8; ++c) {
+        if (!__any_sync(0xffffffffu, und != 0u)) break;
+        const uint4 R = philox_call_pre(w, pre[c], P);
+        apply_planes(R, c, k, und, up, P);
+    }
+    return up | (und & k.F);
 }
 
 // Phase 2: calls 2..7 with the lazy exit; all 32 lanes call it together.

@@ -251,7 +251,7 @@ __device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, uin
         N2 = q[5][i];
     }
     const BlockClass k = block_class(S, N1, N2);
-    const uint32_t res = draw_rest(k, w, und, up, a.hs, P);
+    const uint32_t res = draw_rest_pre(k, w, und, up, a.pre, P);
     if (has) finish_block<HALF, LAYOUT>(a, w, res, S, N1, N2, cnn, acc);
 }
 
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
         }
         const BlockClass k = block_class(S, N1, N2);
         uint32_t und, up;
-        draw_first_two(k, w, 0xffffffffu, a.hs, P, und, up);
+        draw_first_two_pre(k, w, 0xffffffffu, a.pre, P, und, up);
         const bool parked = und != 0u;
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
             const uint32_t w = row * W + col;
             const BlockClass k = block_class(S, N1, N2);
             uint32_t und, up;
-            draw_first_two(k, w, 0xffffffffu, a.hs, a.P, und, up);
+            draw_first_two_pre(k, w, 0xffffffffu, a.pre, a.P, und, up);
             const bool parked = und != 0u;
             const uint32_t mask = __ballot_sync(0xffffffffu, parked);
             if (parked) {
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
             const uint32_t w = row * W + col;
             const BlockClass k = block_class(S, N1, N2);
             uint32_t und, up;
-            draw_first_two(k, w, 0xffffffffu, a.hs, P, und, up);
+            draw_first_two_pre(k, w, 0xffffffffu, a.pre, P, und, up);
             const bool parked = und != 0u;
             const uint32_t mask = __ballot_sync(0xffffffffu, parked);
             if (parked) {
@@ -868,6 +868,23 @@ int blocks_per_sm(const void* kernel, int block) {
     return per_sm;
 }
 
+// Host side of PhiloxPrefix: the uniform words of rounds 1 to 3 of call c.
+static PhiloxPrefix philox_prefix(const DrawParams& P, uint32_t hs, int c) {
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * hs, p1 = (uint64_t)kPhiloxM1 * P.lattice_id;
+    const uint32_t c1 = (uint32_t)p1, c3 = (uint32_t)p0;
+    const uint32_t c2 = (uint32_t)(p0 >> 32) ^ (P.c3_base + (uint32_t)c) ^ P.rk1[0];
+    const uint64_t q1 = (uint64_t)kPhiloxM1 * c2;
+    const uint32_t B = (uint32_t)(q1 >> 32) ^ c1 ^ P.rk0[1];
+    const uint64_t q0 = (uint64_t)kPhiloxM0 * B;
+    PhiloxPrefix u;
+    u.A = (uint32_t)(p1 >> 32) ^ P.rk0[0];
+    u.K2 = c3 ^ P.rk1[1];
+    u.K3 = (uint32_t)q1 ^ P.rk0[2];
+    u.H3 = (uint32_t)(q0 >> 32) ^ P.rk1[2];
+    u.D = (uint32_t)q0;
+    return u;
+}
+
 SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawParams& P,
                      uint32_t hs, long long* oc, long long* op, long long* z) {
     SweepArgs a;
@@ -883,6 +900,7 @@ SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawPa
     a.obs_prev = op;
     a.zero_slot = z;
     a.P = P;
+    for (int c = 0; c < 8; ++c) a.pre[c] = philox_prefix(P, hs, c);
     return a;
 }
 

@@ -240,7 +240,7 @@ __device__ __forceinline__ void cb_drain(const SweepArgs& a, uint32_t* pl, uint3
         k.Cg = q[4][i];
         k.C2 = q[5][i];
     }
-    const uint32_t res = draw_rest(k, d, und, up, a.hs, a.P);
+    const uint32_t res = draw_rest_pre(k, d, und, up, a.pre, a.P);
     if (has) {
         const uint32_t r0 = fdiv(2 * d, a.div_row), r1 = fdiv(2 * d + 1, a.div_row);
         cb_finish<PARITY>(a, pl, d, res, (r0 + PARITY) & 1u, (r1 + PARITY) & 1u, acc, nullptr);
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256, 3) k_checkerboard(const SweepArgs a) {
         c.o0 = c.o1 = 0u;
         if (in) c = cb_block(pl, d, fdiv(2 * d, a.div_row), fdiv(2 * d + 1, a.div_row), a.L, a.Wr, a.nblocks, PARITY);
         uint32_t und, up;
-        draw_first_two(c.k, d, in ? 0xffffffffu : 0u, a.hs, a.P, und, up);
+        draw_first_two_pre(c.k, d, in ? 0xffffffffu : 0u, a.pre, a.P, und, up);
         const bool parked = und != 0u;
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {

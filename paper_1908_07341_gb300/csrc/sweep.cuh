@@ -23,6 +23,7 @@ struct SweepArgs {
     long long* obs_prev;
     long long* zero_slot;
     DrawParams P;
+    PhiloxPrefix pre[8];  // round prefixes of the 8 Philox calls of half-step hs
 };
 
 // ------------------------------------------------------------ neighbour gathers
