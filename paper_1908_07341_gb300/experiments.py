@@ -31,11 +31,12 @@ def grid_points(n: int, upper: float) -> np.ndarray:
 def critical_curve_sweep(L: int = 224, n_grid: int = 80, q_max: float = 2.0, J_max: float = 2.0,
                          warmup: int = 300_000, measured: int = 300_000, seed: int = 1,
                          steps_per_launch: int = 8, block_threads: int = 256, tile_sites: int = 1 << 18,
-                         device="cuda") -> dict:
+                         var_threshold: float = 0.03, device="cuda") -> dict:
     """One lattice per grid point (q_i, J_j), all spins -1 at the start,
     `warmup` steps, then the statistics of `measured` more steps.  Returns the
-    grids of <m>, Var m and <|m|>, the J of the largest Var m for every q, and
-    the timing."""
+    grids of <m>, Var m and <|m|>, the J of the largest Var m for every q, the
+    first J with Var m >= var_threshold for every q (the cells the paper's
+    figures mark), and the timing."""
     q = grid_points(n_grid, q_max)
     J = grid_points(n_grid, J_max)
     Q, JJ = np.meshgrid(q, J, indexing="ij")
@@ -55,8 +56,12 @@ def critical_curve_sweep(L: int = 224, n_grid: int = 80, q_max: float = 2.0, J_m
     d = derived(stats, np.full(n, L), Q.ravel(), JJ.ravel())
     var_m = d["var_m"].reshape(n_grid, n_grid)
     peak_J = J[np.argmax(var_m, axis=1)]
+    # the paper's figures mark the cells with Var m >= 0.03; the first such J per q
+    above = var_m >= var_threshold
+    first_J = np.where(above.any(axis=1), J[np.argmax(above, axis=1)], np.nan)
     return {"L": L, "q": q, "J": J, "mean_m": d["m"].reshape(n_grid, n_grid), "var_m": var_m,
             "abs_m": d["abs_m"].reshape(n_grid, n_grid), "peak_J": peak_J, "J_c": critical_J(q),
+            "var_threshold": var_threshold, "first_J_above_threshold": first_J,
             "stats": stats, "wall_s": wall,
             "site_updates": float(n) * 2.0 * L * L * total,
             "rate": float(n) * 2.0 * L * L * total / wall}
