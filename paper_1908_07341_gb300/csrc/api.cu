@@ -241,6 +241,7 @@ static bool checkerboard_draw_params(double J, uint64_t seed, uint32_t lattice_i
 
 int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
                          uint64_t n_steps, int64_t* dev_obs, void* stream) {
+    const TraceRange trace("shk_checkerboard_run");
     Geometry g;
     if (!make_geometry(L, kBitpack, &g))
         return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
@@ -305,6 +306,7 @@ size_t shk_coalescence_scratch_bytes(int n_pairs) {
 int shk_coalescence_times(int dynamics, int n_pairs, const int* L, const double* q, const double* J,
                           const uint64_t* seed, const uint32_t* lattice_id, uint64_t max_steps, void* dev_scratch,
                           size_t bytes, uint64_t* host_T, void* stream) {
+    const TraceRange trace("shk_coalescence_times");
     if (!dev_scratch || !host_T) return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: bad argument");
     if (max_steps == 0 || max_steps >= SHK_MAX_STEP)
         return fail(nullptr, SHK_EINVAL, "shk_coalescence_times: max_steps must be in 1..2^31-1");
@@ -336,6 +338,7 @@ size_t shk_cftp_scratch_bytes(int n_pairs) {
 int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const double* J, const uint64_t* seed,
              const uint32_t* lattice_id, int k_max, void* dev_samples, size_t sample_stride_bytes,
              void* dev_scratch, size_t bytes, int32_t* host_k, void* stream) {
+    const TraceRange trace("shk_cftp");
     if (!dev_samples || !dev_scratch || !host_k) return fail(nullptr, SHK_EINVAL, "shk_cftp: bad argument");
     if (k_max < 0 || k_max > SHK_CFTP_MAX_K)
         return fail(nullptr, SHK_EINVAL, "shk_cftp: k_max=%d outside 0..%d", k_max, SHK_CFTP_MAX_K);
@@ -458,6 +461,7 @@ int shk_get_step(const shk_lattice* lat, uint64_t* step) {
 }
 
 int shk_run(shk_lattice* lat, uint64_t n_steps, int64_t* dev_obs) {
+    const TraceRange trace("shk_run");
     if (lat == nullptr) return fail(nullptr, SHK_EINVAL, "shk_run: NULL handle");
     if (!lat->params_set) return fail(lat, SHK_ESTATE, "shk_run: call shk_set_params first");
     if (n_steps == 0) return SHK_OK;

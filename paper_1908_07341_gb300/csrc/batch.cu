@@ -632,6 +632,7 @@ int shk_batch_init(shk_batch* b, int kind, uint64_t init_seed) {
 }
 
 int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
+    const TraceRange trace("shk_batch_run");
     if (!b) return bfail(nullptr, SHK_EINVAL, "shk_batch_run: NULL handle");
     if (n_steps == 0) return SHK_OK;
     if (b->step + n_steps > SHK_MAX_STEP)
@@ -1006,6 +1007,7 @@ int shk_server_cancel(shk_server* s, uint64_t job_id) {
 }
 
 int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
+    const TraceRange trace("shk_server_tick");
     if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_tick: NULL handle");
     cudaError_t e = cudaSuccess;
     // (1) admission, oldest first, while a slot is free and the job fits

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "device.cuh"
 
@@ -90,5 +91,14 @@ int sm_count();
 
 // Message returned by shk_last_error(NULL) on this host thread.
 void set_thread_error(const char* msg);
+
+// Named range on the host timeline for profilers that record NVTX (no-op
+// when no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 }  // namespace shk

@@ -8,6 +8,7 @@ only marshals jobs and results and keeps the wall clock for latencies.
 from __future__ import annotations
 
 import ctypes
+import json
 import time
 
 import numpy as np
@@ -50,7 +51,10 @@ def fnv1a64(data: bytes) -> int:
 
 class Server:
     def __init__(self, max_slots: int, arena_bytes: int, hbm_budget: int | None = None, device="cuda",
-                 stream=None):
+                 stream=None, result_log: str | None = None):
+        """result_log: optional path; every result poll() returns is also
+        appended to it as one JSON line."""
+        self.result_log = result_log
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         nbytes = int(lib().shk_server_bytes(int(max_slots), int(arena_bytes)))
@@ -108,6 +112,11 @@ class Server:
                         "stats": np.array(r.stats[:], dtype=np.int64),
                         "last_obs": np.array(r.last_obs[:], dtype=np.int64), "sigma_hash": r.sigma_hash,
                         "submit_tick": r.submit_tick, "admit_tick": r.admit_tick, "done_tick": r.done_tick})
+        if self.result_log and out:
+            with open(self.result_log, "a") as f:
+                for r in out:
+                    f.write(json.dumps({k: (v.tolist() if isinstance(v, np.ndarray) else int(v))
+                                        for k, v in r.items()}) + "\n")
         return out
 
     def stats(self):

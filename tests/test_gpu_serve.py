@@ -141,3 +141,22 @@ def test_deadlines_expire_queued_and_running_jobs():
     assert got[c]["status"] == 0 and got[c]["steps_done"] == 8 and got[c]["admit_tick"] == 3
     stats, last, h = _single(jc)
     assert np.array_equal(got[c]["stats"], stats) and got[c]["sigma_hash"] == h
+
+
+def test_result_log_lines(tmp_path):
+    import json
+    log = tmp_path / "results.jsonl"
+    srv = Server(max_slots=2, arena_bytes=8 << 20, result_log=str(log)).configure(steps_per_launch=2,
+                                                                                 launches_per_tick=2)
+    ids = [srv.submit(**JOBS[2]), srv.submit(**JOBS[7])]
+    got = []
+    for _ in range(10):
+        srv.tick()
+        got += srv.poll()
+        if len(got) == 2:
+            break
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert sorted(r["job_id"] for r in lines) == sorted(ids)
+    for r in lines:
+        want = next(g for g in got if g["job_id"] == r["job_id"])
+        assert r["stats"] == want["stats"].tolist() and r["sigma_hash"] == want["sigma_hash"]
