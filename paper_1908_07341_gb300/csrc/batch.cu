@@ -51,6 +51,8 @@ struct BatchLattice {
     unsigned long long burn_in;        // steps t < burn_in are not added to the statistics
     uint32_t parity;                   // sigma buffer holding the current state (flipped on the device)
     uint32_t pad;
+    FastDiv div_wr;                    // division by Wr
+    uint32_t pad2;
     DrawParams P;
 };
 
@@ -77,25 +79,30 @@ struct BatchArgs {
     long long* last_obs;           // n_lattices x 5
 };
 
+// Global row of local row rho of a tile whose first row is r_base: r_base is
+// at least -32 (the halo below row 0) and r_base + rho stays below 2L, so one
+// wrap each way is enough.
+__device__ __forceinline__ uint32_t global_row(int32_t r_base, uint32_t rho, uint32_t L) {
+    int32_t g = r_base + (int32_t)rho;
+    if (g < 0) g += (int32_t)L;
+    else if (g >= (int32_t)L) g -= (int32_t)L;
+    return (uint32_t)g;
+}
+
 // Draws rows [rlo, rhi) of dst (local row index) from src in shared memory.
 // HALF 0 reads the row below (rho - 1), HALF 1 the row above (rho + 1); the
 // left/right neighbour wraps within the row.  Random numbers use the global
 // block index (global row g = (r_base + rho) mod L).
 template <int HALF, int BLOCK>
 __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, uint32_t rlo, uint32_t rhi,
-                                           uint32_t R, bool wrap, uint32_t Wr, uint32_t L, int64_t r_base,
-                                           uint32_t hs, const DrawParams& P, uint32_t (*q)[kQueueCap]) {
+                                           uint32_t R, bool wrap, uint32_t Wr, const FastDiv& dw, uint32_t L,
+                                           int32_t r_base, uint32_t hs, const DrawParams& P,
+                                           uint32_t (*q)[kQueueCap]) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lo = rlo * Wr, hi = rhi * Wr;
     const uint32_t below = (1u << lane) - 1u;
     uint32_t head = 0;
     int count = 0;
-    auto global_block = [&](uint32_t i) -> uint32_t {
-        const uint32_t rho = i / Wr, c = i - rho * Wr;
-        int64_t g = (r_base + (int64_t)rho) % (int64_t)L;
-        if (g < 0) g += L;
-        return (uint32_t)g * Wr + c;
-    };
     auto drain = [&](int n) {
         const bool has = (int)lane < n;
         const uint32_t e = (head + lane) & (kQueueCap - 1);
@@ -111,7 +118,7 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
         const bool in = i < hi;
         uint32_t S = 0, N1 = 0, N2 = 0, w = 0;
         if (in) {
-            const uint32_t rho = i / Wr, c = i - rho * Wr;
+            const uint32_t rho = fdiv(i, dw), c = i - rho * Wr;
             S = src[i];
             if (HALF == 0) {
                 N1 = src[(rho == 0 && wrap ? R - 1 : rho - 1) * Wr + c];
@@ -122,7 +129,7 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
                 const uint32_t next = src[rho * Wr + (c + 1 == Wr ? 0 : c + 1)];
                 N2 = (S >> 1) | (next << 31);
             }
-            w = global_block(i);
+            w = (uint32_t)global_row(r_base, rho, L) * Wr + c;
         }
         const BlockClass k = block_class(S, N1, N2);
         uint32_t und, up;
@@ -193,7 +200,8 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         // otherwise the tile carries rows r0-k .. r0+Hloc+k (k below, k+1 above).
         const bool wrap = it.ntiles == 1;
         const uint32_t R = wrap ? L : Hloc + 2 * k + 1;
-        const int64_t r_base = wrap ? 0 : (int64_t)r0 - (int64_t)k;
+        const int32_t r_base = wrap ? 0 : (int32_t)r0 - (int32_t)k;
+        const FastDiv dw = B->div_wr;
         const uint32_t own_lo = wrap ? 0 : k;           // local rows of the tile itself
         const uint32_t sweep_lo = wrap ? 0 : 1;
         {
@@ -205,23 +213,21 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         uint32_t* tu = tile_mem + R * Wr;
         const uint32_t* sig_in = reinterpret_cast<const uint32_t*>(a.arena + B->sigma_off[par]);
         for (uint32_t x = tid; x < R * Wr; x += BLOCK) {
-            const uint32_t rho = x / Wr, c = x - rho * Wr;
-            int64_t g = (r_base + (int64_t)rho) % (int64_t)L;
-            if (g < 0) g += L;
-            sg[x] = sig_in[(size_t)g * Wr + c];
+            const uint32_t rho = fdiv(x, dw), c = x - rho * Wr;
+            sg[x] = sig_in[(size_t)global_row(r_base, rho, L) * Wr + c];
         }
         __syncthreads();
         long long* partial = reinterpret_cast<long long*>(a.arena + B->scratch_off);
         for (uint32_t j = 0; j < k; ++j) {
             const uint32_t hs = (uint32_t)(2 * (t0 + j));
-            tile_sweep<0, BLOCK>(sg, tu, sweep_lo, R, R, wrap, Wr, L, r_base, hs, P, q);
+            tile_sweep<0, BLOCK>(sg, tu, sweep_lo, R, R, wrap, Wr, dw, L, r_base, hs, P, q);
             __syncthreads();
-            tile_sweep<1, BLOCK>(tu, sg, sweep_lo, wrap ? R : R - 1, R, wrap, Wr, L, r_base, hs + 1, P, q);
+            tile_sweep<1, BLOCK>(tu, sg, sweep_lo, wrap ? R : R - 1, R, wrap, Wr, dw, L, r_base, hs + 1, P, q);
             __syncthreads();
             // sums over the tile's own rows
             int v[kNumObs] = {0, 0, 0, 0, 0};
             for (uint32_t x = own_lo * Wr + tid; x < (own_lo + Hloc) * Wr; x += BLOCK) {
-                const uint32_t rho = x / Wr, c = x - rho * Wr;
+                const uint32_t rho = fdiv(x, dw), c = x - rho * Wr;
                 const uint32_t cr = rho * Wr + (c + 1 == Wr ? 0 : c + 1);
                 const uint32_t xu = (rho + 1 == R && wrap ? 0 : rho + 1) * Wr + c;
                 const uint32_t s = sg[x], t = tu[x];
@@ -550,6 +556,7 @@ int shk_batch_create(int n, const int* L, const double* q, const double* J, cons
         std::memset(&B, 0, sizeof B);
         B.L = (uint32_t)L[i];
         B.Wr = g.Wr;
+        B.div_wr = make_fastdiv(g.Wr);
         B.sigma_off[0] = lat_off[i];
         B.sigma_off[1] = lat_off[i] + g.plane_bytes;
         B.tau_off = lat_off[i] + 2 * g.plane_bytes;
@@ -1040,6 +1047,7 @@ int shk_server_tick(shk_server* s, int* n_active, int* n_pending) {
         std::memset(&B, 0, sizeof B);
         B.L = (uint32_t)p.job.L;
         B.Wr = g.Wr;
+        B.div_wr = make_fastdiv(g.Wr);
         const size_t base = s->off_arena + off;
         B.sigma_off[0] = base;
         B.sigma_off[1] = base + g.plane_bytes;
