@@ -32,7 +32,8 @@ struct CorrArgs {
 // Bits of sites (i + l .. i + l + 31, row) for the block whose first site is
 // i = 32 c, read from a bit-packed row with wrap-around.
 __device__ __forceinline__ uint32_t shifted_row_word(const uint32_t* row, uint32_t c, uint32_t l, uint32_t Wr) {
-    const uint32_t cw = (c + (l >> 5)) % Wr;
+    uint32_t cw = c + (l >> 5);     // c < Wr and l < L, so below 2 Wr
+    if (cw >= Wr) cw -= Wr;
     const uint32_t sh = l & 31u;
     const uint32_t lo = row[cw];
     if (sh == 0) return lo;
@@ -307,6 +308,8 @@ __global__ void __launch_bounds__(256, 3) k_checkerboard(const SweepArgs a) {
 struct CoalescePair {
     uint32_t L, Wr, nblocks;
     uint32_t pad;
+    FastDiv div_wr;     // division by Wr
+    uint32_t pad2;
     DrawParams P;
 };
 
@@ -329,9 +332,10 @@ struct CftpArgs {
 // Bits of block w and of its two field neighbours in a bit-packed shared-
 // memory plane (rows of Wr words, L rows, wrapping).
 template <int HALF>
-__device__ __forceinline__ void smem_fields(const uint32_t* pl, uint32_t w, uint32_t Wr, uint32_t L,
-                                            uint32_t nblocks, uint32_t& S, uint32_t& N1, uint32_t& N2) {
-    const uint32_t row = w / Wr, col = w - row * Wr;
+__device__ __forceinline__ void smem_fields(const uint32_t* pl, uint32_t w, uint32_t Wr, const FastDiv& dw,
+                                            uint32_t L, uint32_t nblocks, uint32_t& S, uint32_t& N1,
+                                            uint32_t& N2) {
+    const uint32_t row = fdiv(w, dw), col = w - row * Wr;
     words_aligned<HALF>(pl, w, row, col, L, Wr, nblocks, S, N1, N2);
 }
 
@@ -340,6 +344,7 @@ __device__ __forceinline__ void smem_fields(const uint32_t* pl, uint32_t w, uint
 struct PairPlanes {
     uint32_t *st, *tt, *sb, *tb;
     uint32_t nb, nbp, Wr, L;
+    FastDiv dw;
 };
 
 __device__ __forceinline__ PairPlanes pair_planes(uint32_t* smem, const CoalescePair& cp) {
@@ -348,6 +353,7 @@ __device__ __forceinline__ PairPlanes pair_planes(uint32_t* smem, const Coalesce
     p.nbp = (cp.nblocks + 31u) & ~31u;
     p.Wr = cp.Wr;
     p.L = cp.L;
+    p.dw = cp.div_wr;
     p.st = smem;
     p.tt = smem + p.nbp;
     p.sb = smem + 2 * p.nbp;
@@ -398,11 +404,11 @@ __device__ __forceinline__ void pair_step(const PairPlanes& p, unsigned long lon
                 if (in) {
                     uint32_t S0, A0, B0, S1, A1, B1;
                     if (half == 0) {
-                        smem_fields<0>(p.st, w, p.Wr, p.L, p.nb, S0, A0, B0);
-                        smem_fields<0>(p.sb, w, p.Wr, p.L, p.nb, S1, A1, B1);
+                        smem_fields<0>(p.st, w, p.Wr, p.dw, p.L, p.nb, S0, A0, B0);
+                        smem_fields<0>(p.sb, w, p.Wr, p.dw, p.L, p.nb, S1, A1, B1);
                     } else {
-                        smem_fields<1>(p.tt, w, p.Wr, p.L, p.nb, S0, A0, B0);
-                        smem_fields<1>(p.tb, w, p.Wr, p.L, p.nb, S1, A1, B1);
+                        smem_fields<1>(p.tt, w, p.Wr, p.dw, p.L, p.nb, S0, A0, B0);
+                        smem_fields<1>(p.tb, w, p.Wr, p.dw, p.L, p.nb, S1, A1, B1);
                     }
                     k[0] = block_class(S0, A0, B0);
                     k[1] = block_class(S1, A1, B1);
@@ -427,7 +433,7 @@ __device__ __forceinline__ void pair_step(const PairPlanes& p, unsigned long lon
                 c0.k = c1.k = {0u, 0u, 0u};
                 c0.o0 = c0.o1 = 0u;
                 if (in) {
-                    const uint32_t r0 = (2 * d) / p.Wr, r1 = (2 * d + 1) / p.Wr;
+                    const uint32_t r0 = fdiv(2 * d, p.dw), r1 = fdiv(2 * d + 1, p.dw);
                     c0 = cb_block(p.st, d, r0, r1, p.L, p.Wr, p.nb, (uint32_t)half);
                     c1 = cb_block(p.sb, d, r0, r1, p.L, p.Wr, p.nb, (uint32_t)half);
                 }
@@ -582,6 +588,8 @@ void fill_coalesce_pair(void* dst, int L, const DrawParams& P) {
     c->Wr = (uint32_t)L / 32;
     c->nblocks = (uint32_t)((int64_t)L * L / 32);
     c->pad = 0;
+    c->div_wr = make_fastdiv(c->Wr);
+    c->pad2 = 0;
     c->P = P;
 }
 
