@@ -103,6 +103,16 @@ const char* shk_last_error(const void* handle);
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int shk_version(void);
 
+/* Bounds checks of the debug build (libshaken built with -DSHK_DEBUG_BOUNDS,
+ * build.py --debug-bounds): every global-memory access of the kernels checks
+ * its index against its buffer; the first access out of range is recorded and
+ * redirected to the buffer's first element, so no kernel faults.  *first_site
+ * receives that access's site, translation unit << 16 | source line (units:
+ * 1 sweeps, 2 batch and serving, 3 Section 3 kernels), or 0 if none, and the
+ * record is cleared.  Synchronises the device.  SHK_ESTATE in the normal
+ * build (*first_site = 0). */
+int shk_debug_bounds(uint32_t* first_site);
+
 /* ------------------------------------------------------------ thresholds */
 
 /* The six integer thresholds of the per-site draw (Algorithm 3: "+1 iff

@@ -11,7 +11,9 @@ import functools
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libshaken.so")
+# SHK_LIBRARY selects another build of the same library, e.g. the bounds-checked
+# libshaken_debug.so (build.py --debug-bounds).
+LIB_PATH = os.environ.get("SHK_LIBRARY") or os.path.join(_PKG, "libshaken.so")
 
 # status codes and enums (mirrors of include/shaken.h)
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, EBUSY, ETIMEOUT, ECANCELLED = 0, -1, -2, -3, -4, -5, -6, -7
@@ -46,6 +48,7 @@ SIGNATURES = {
     "shk_coalescence_times": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _sz, _vp, _vp]),
     "shk_cftp_scratch_bytes": (_sz, [_i]),
     "shk_philox_peak": (_i, [_i, _u32, _vp, _vp]),
+    "shk_debug_bounds": (_i, [_vp]),
     "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),
     "shk_checkerboard_thresholds": (_i, [_d, _vp]),
     "shk_checkerboard_run": (_i, [_vp, _i, _d, _u64, _u32, _u64, _u64, _vp, _vp]),

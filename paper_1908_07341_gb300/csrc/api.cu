@@ -15,6 +15,7 @@
 
 #include "shaken.h"
 #include "internal.h"
+#include "bounds.cuh"
 
 namespace shk {
 
@@ -157,6 +158,17 @@ const char* shk_last_error(const void* handle) {
 }
 
 int shk_version(void) { return 100; }
+
+int shk_debug_bounds(uint32_t* first_site) {
+    if (first_site == nullptr) return fail(nullptr, SHK_EINVAL, "shk_debug_bounds: first_site is NULL");
+    *first_site = 0;
+    if (!kBoundsChecked)
+        return fail(nullptr, SHK_ESTATE, "shk_debug_bounds: the library was built without bounds checks");
+    const unsigned sites[3] = {bounds_site_kernels(), bounds_site_batch(), bounds_site_sampling()};
+    for (unsigned v : sites)
+        if (v != 0 && *first_site == 0) *first_site = v;
+    return SHK_OK;
+}
 
 int shk_thresholds(double q, double J, uint32_t out[6]) {
     const int rc = host_thresholds(q, J, out);

@@ -32,7 +32,9 @@
 #include <vector>
 
 #include "shaken.h"
+#define SHK_TU_ID 2
 #include "internal.h"
+#include "bounds.cuh"
 
 namespace shk {
 
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         const uint32_t* sig_in = reinterpret_cast<const uint32_t*>(a.arena + B->sigma_off[par]);
         for (uint32_t x = tid; x < R * Wr; x += BLOCK) {
             const uint32_t rho = fdiv(x, dw), c = x - rho * Wr;
-            sg[x] = sig_in[(size_t)global_row(r_base, rho, L) * Wr + c];
+            sg[x] = *checked(sig_in, (uint64_t)global_row(r_base, rho, L) * Wr + c, (uint64_t)L * Wr, SHK_SITE);
         }
         __syncthreads();
         long long* partial = reinterpret_cast<long long*>(a.arena + B->scratch_off);
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         for (uint32_t x = tid; x < Hloc * Wr; x += BLOCK) {
             const uint32_t lx = x + own_lo * Wr;
             const size_t gx = (size_t)r0 * Wr + x;
-            sig_out[gx] = sg[lx];
-            tau_out[gx] = tu[lx];
+            *checked(sig_out, gx, (uint64_t)L * Wr, SHK_SITE) = sg[lx];
+            *checked(tau_out, gx, (uint64_t)L * Wr, SHK_SITE) = tu[lx];
         }
         // the last tile of this lattice folds the k steps into the statistics
         __syncthreads();
@@ -320,6 +322,10 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
     }
 }
 
+}  // namespace shk
+
+namespace shk {
+unsigned bounds_site_batch() { return take_bounds_site(); }
 }  // namespace shk
 
 using namespace shk;

@@ -92,6 +92,12 @@ int sm_count();
 // Message returned by shk_last_error(NULL) on this host thread.
 void set_thread_error(const char* msg);
 
+// First bounds-check failure site recorded by each translation unit in the
+// debug build (0 = none; always 0 in the normal build), cleared on read.
+unsigned bounds_site_kernels();
+unsigned bounds_site_batch();
+unsigned bounds_site_sampling();
+
 // Named range on the host timeline for profilers that record NVTX (no-op
 // when no tool is attached).
 struct TraceRange {

@@ -25,6 +25,7 @@
 #include <mutex>
 #include <unordered_map>
 
+#define SHK_TU_ID 1
 #include "internal.h"
 #include "sweep.cuh"
 
@@ -75,13 +76,13 @@ __device__ __forceinline__ RawBp load_bp(const uint32_t* __restrict__ src, uint3
     const uint32_t row = fdiv(w, a.div_row);
     const uint32_t col = w - row * a.Wr;
     RawBp r;
-    r.s = __ldg(src + w);
+    r.s = __ldg(checked(src, w, a.nblocks, SHK_SITE));
     if (HALF == 0) {
-        r.n = __ldg(src + (row > 0 ? w - a.Wr : w + a.nblocks - a.Wr));
-        r.x = __ldg(src + (col > 0 ? w - 1 : w + a.Wr - 1));
+        r.n = __ldg(checked(src, row > 0 ? w - a.Wr : w + a.nblocks - a.Wr, a.nblocks, SHK_SITE));
+        r.x = __ldg(checked(src, col > 0 ? w - 1 : w + a.Wr - 1, a.nblocks, SHK_SITE));
     } else {
-        r.n = __ldg(src + (row + 1 < a.L ? w + a.Wr : w + a.Wr - a.nblocks));
-        r.x = __ldg(src + (col + 1 < a.Wr ? w + 1 : w + 1 - a.Wr));
+        r.n = __ldg(checked(src, row + 1 < a.L ? w + a.Wr : w + a.Wr - a.nblocks, a.nblocks, SHK_SITE));
+        r.x = __ldg(checked(src, col + 1 < a.Wr ? w + 1 : w + 1 - a.Wr, a.nblocks, SHK_SITE));
     }
     return r;
 }
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_bp(const SweepArgs a) {
 #pragma unroll
         for (int k = 0; k < ILP; ++k) {
             if (valid[k]) {
-                dst[w[k]] = up[k];
+                *checked(dst, w[k], a.nblocks, SHK_SITE) = up[k];
                 accumulate_step<HALF>(acc, up[k], S[k], N1[k], N2[k], 0xffffffffu, cnn);
             }
         }
@@ -156,18 +157,18 @@ __device__ __forceinline__ RawI8 load_i8(const int8_t* __restrict__ src, uint32_
     const uint32_t row = fdiv(w, a.div_row);
     const uint32_t col = w - row * a.Wr;
     RawI8 r;
-    const uint4* s4 = reinterpret_cast<const uint4*>(src + 32 * (size_t)w);
-    r.s0 = __ldg(s4);
-    r.s1 = __ldg(s4 + 1);
+    const uint4* q4 = reinterpret_cast<const uint4*>(src);      // 16-byte chunks, two per block
+    const uint64_t n4 = 2 * (uint64_t)a.nblocks;
+    r.s0 = __ldg(checked(q4, 2 * (uint64_t)w, n4, SHK_SITE));
+    r.s1 = __ldg(checked(q4, 2 * (uint64_t)w + 1, n4, SHK_SITE));
     const uint32_t wn = HALF == 0 ? (row > 0 ? w - a.Wr : w + a.nblocks - a.Wr)
                                   : (row + 1 < a.L ? w + a.Wr : w + a.Wr - a.nblocks);
-    const uint4* n4 = reinterpret_cast<const uint4*>(src + 32 * (size_t)wn);
-    r.n0 = __ldg(n4);
-    r.n1 = __ldg(n4 + 1);
+    r.n0 = __ldg(checked(q4, 2 * (uint64_t)wn, n4, SHK_SITE));
+    r.n1 = __ldg(checked(q4, 2 * (uint64_t)wn + 1, n4, SHK_SITE));
     size_t idx;
     if (HALF == 0) idx = col > 0 ? 32 * (size_t)w - 1 : 32 * (size_t)w + a.L - 1;
     else idx = col + 1 < a.Wr ? 32 * (size_t)w + 32 : 32 * (size_t)w + 32 - a.L;
-    r.x = __ldg(src + idx);
+    r.x = __ldg(checked(src, idx, 32 * (uint64_t)a.nblocks, SHK_SITE));
     return r;
 }
 
@@ -202,9 +203,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_i8a(const SweepArgs a) {
         const uint32_t up = draw_block(S, N1, N2, w, 0xffffffffu, a.hs, a.P);
         uint4 lo, hi;
         unpack32(up, lo, hi);
-        uint4* d4 = reinterpret_cast<uint4*>(dst + 32 * (size_t)w);
-        d4[0] = lo;
-        d4[1] = hi;
+        uint4* q4 = reinterpret_cast<uint4*>(dst);
+        *checked(q4, 2 * (uint64_t)w, 2 * (uint64_t)a.nblocks, SHK_SITE) = lo;
+        *checked(q4, 2 * (uint64_t)w + 1, 2 * (uint64_t)a.nblocks, SHK_SITE) = hi;
         accumulate_step<HALF>(acc, up, S, N1, N2, 0xffffffffu, cnn);
     }
     finish_step<HALF>(acc, a);
@@ -223,13 +224,13 @@ template <int HALF, int LAYOUT>
 __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uint32_t up, uint32_t S,
                                              uint32_t N1, uint32_t N2, bool cnn, int (&acc)[3]) {
     if (LAYOUT == kBitpack) {
-        static_cast<uint32_t*>(a.dst)[w] = up;
+        *checked(static_cast<uint32_t*>(a.dst), w, a.nblocks, SHK_SITE) = up;
     } else {
         uint4 lo, hi;
         unpack32(up, lo, hi);
-        uint4* d4 = reinterpret_cast<uint4*>(static_cast<int8_t*>(a.dst) + 32 * (size_t)w);
-        d4[0] = lo;
-        d4[1] = hi;
+        uint4* q4 = reinterpret_cast<uint4*>(a.dst);
+        *checked(q4, 2 * (uint64_t)w, 2 * (uint64_t)a.nblocks, SHK_SITE) = lo;
+        *checked(q4, 2 * (uint64_t)w + 1, 2 * (uint64_t)a.nblocks, SHK_SITE) = hi;
     }
     accumulate_step<HALF>(acc, up, S, N1, N2, 0xffffffffu, cnn);
 }
@@ -338,14 +339,14 @@ struct RowRaw<kInt8> {
 };
 
 template <int LAYOUT>
-__device__ __forceinline__ RowRaw<LAYOUT> load_row(const void* src, uint32_t w) {
+__device__ __forceinline__ RowRaw<LAYOUT> load_row(const void* src, uint32_t w, uint32_t nblocks) {
     RowRaw<LAYOUT> r;
     if constexpr (LAYOUT == kBitpack) {
-        r.v = __ldg(static_cast<const uint32_t*>(src) + w);
+        r.v = __ldg(checked(static_cast<const uint32_t*>(src), w, nblocks, SHK_SITE));
     } else {
-        const uint4* p = reinterpret_cast<const uint4*>(static_cast<const int8_t*>(src) + 32 * (size_t)w);
-        r.lo = __ldg(p);
-        r.hi = __ldg(p + 1);
+        const uint4* q4 = reinterpret_cast<const uint4*>(src);
+        r.lo = __ldg(checked(q4, 2 * (uint64_t)w, 2 * (uint64_t)nblocks, SHK_SITE));
+        r.hi = __ldg(checked(q4, 2 * (uint64_t)w + 1, 2 * (uint64_t)nblocks, SHK_SITE));
     }
     return r;
 }
@@ -359,14 +360,15 @@ __device__ __forceinline__ uint32_t row_bits(const RowRaw<LAYOUT>& r) {
 // The field-neighbour bit just outside the strip in row `row`: bit 31 of the
 // block left of the strip (A) or bit 0 of the block right of it (B).
 template <int HALF, int LAYOUT>
-__device__ __forceinline__ uint32_t edge_bit(const void* src, uint32_t row, uint32_t edge_block, uint32_t W) {
+__device__ __forceinline__ uint32_t edge_bit(const void* src, uint32_t row, uint32_t edge_block, uint32_t W,
+                                             uint32_t nblocks) {
     const size_t b = (size_t)row * W + edge_block;
     if constexpr (LAYOUT == kBitpack) {
-        const uint32_t v = __ldg(static_cast<const uint32_t*>(src) + b);
+        const uint32_t v = __ldg(checked(static_cast<const uint32_t*>(src), b, nblocks, SHK_SITE));
         return HALF == 0 ? v >> 31 : v & 1u;
     } else {
         const int8_t* p = static_cast<const int8_t*>(src);
-        return (uint32_t)(__ldg(p + 32 * b + (HALF == 0 ? 31 : 0)) > 0);
+        return (uint32_t)(__ldg(checked(p, 32 * b + (HALF == 0 ? 31 : 0), 32 * (uint64_t)nblocks, SHK_SITE)) > 0);
     }
 }
 
@@ -406,17 +408,17 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
         auto row_at = [&](uint32_t i) -> uint32_t { return HALF == 0 ? r0 + i : r0 + nrows - 1 - i; };
         const uint32_t first = row_at(0);
         const uint32_t nb_row = HALF == 0 ? (first == 0 ? L - 1 : first - 1) : (first + 1 == L ? 0 : first + 1);
-        uint32_t prev = row_bits<LAYOUT>(load_row<LAYOUT>(a.src, nb_row * W + col));
-        RowRaw<LAYOUT> cur = load_row<LAYOUT>(a.src, first * W + col);
-        uint32_t cur_edge = edge_lane ? edge_bit<HALF, LAYOUT>(a.src, first, edge_block, W) : 0u;
+        uint32_t prev = row_bits<LAYOUT>(load_row<LAYOUT>(a.src, nb_row * W + col, a.nblocks));
+        RowRaw<LAYOUT> cur = load_row<LAYOUT>(a.src, first * W + col, a.nblocks);
+        uint32_t cur_edge = edge_lane ? edge_bit<HALF, LAYOUT>(a.src, first, edge_block, W, a.nblocks) : 0u;
         for (uint32_t i = 0; i < nrows; ++i) {
             const uint32_t row = row_at(i);
             RowRaw<LAYOUT> nxt{};
             uint32_t nxt_edge = 0;
             if (i + 1 < nrows) {                                      // prefetch the next row
                 const uint32_t r = row_at(i + 1);
-                nxt = load_row<LAYOUT>(a.src, r * W + col);
-                if (edge_lane) nxt_edge = edge_bit<HALF, LAYOUT>(a.src, r, edge_block, W);
+                nxt = load_row<LAYOUT>(a.src, r * W + col, a.nblocks);
+                if (edge_lane) nxt_edge = edge_bit<HALF, LAYOUT>(a.src, r, edge_block, W, a.nblocks);
             }
             const uint32_t S = row_bits<LAYOUT>(cur), N1 = prev;
             uint32_t N2;
@@ -512,20 +514,22 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
                 const size_t b = (size_t)r * W + col;
                 uint32_t* dst = &ring[wib][i % DEPTH][lane * NW];
                 if constexpr (LAYOUT == kBitpack) {
-                    cp_async4(dst, static_cast<const uint32_t*>(a.src) + b);
+                    cp_async4(dst, checked(static_cast<const uint32_t*>(a.src), b, a.nblocks, SHK_SITE));
                 } else {
-                    const int8_t* g = static_cast<const int8_t*>(a.src) + 32 * b;
-                    cp_async16(dst, g);
-                    cp_async16(dst + 4, g + 16);
+                    const uint4* q4 = reinterpret_cast<const uint4*>(a.src);
+                    cp_async16(dst, checked(q4, 2 * b, 2 * (uint64_t)a.nblocks, SHK_SITE));
+                    cp_async16(dst + 4, checked(q4, 2 * b + 1, 2 * (uint64_t)a.nblocks, SHK_SITE));
                 }
                 if (edge_lane) {
                     const size_t eb = (size_t)r * W + edge_block;
                     if constexpr (LAYOUT == kBitpack) {
-                        cp_async4(&ring_edge[wib][i % DEPTH][0], static_cast<const uint32_t*>(a.src) + eb);
+                        cp_async4(&ring_edge[wib][i % DEPTH][0],
+                                  checked(static_cast<const uint32_t*>(a.src), eb, a.nblocks, SHK_SITE));
                     } else {
                         // the 4-byte word holding the byte next to the strip
-                        const int8_t* g = static_cast<const int8_t*>(a.src) + 32 * eb + (HALF == 0 ? 28 : 0);
-                        cp_async4(&ring_edge[wib][i % DEPTH][0], g);
+                        const uint32_t* q1 = reinterpret_cast<const uint32_t*>(a.src);
+                        cp_async4(&ring_edge[wib][i % DEPTH][0],
+                                  checked(q1, 8 * eb + (HALF == 0 ? 7 : 0), 8 * (uint64_t)a.nblocks, SHK_SITE));
                     }
                 }
             }
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
         };
         const uint32_t first = row_at(0);
         const uint32_t nb_row = HALF == 0 ? (first == 0 ? L - 1 : first - 1) : (first + 1 == L ? 0 : first + 1);
-        uint32_t prev = row_bits<LAYOUT>(load_row<LAYOUT>(a.src, nb_row * W + col));
+        uint32_t prev = row_bits<LAYOUT>(load_row<LAYOUT>(a.src, nb_row * W + col, a.nblocks));
         __syncwarp();
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) stage(d);
@@ -623,7 +627,8 @@ __global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {
         const uint32_t up = draw_block(S, N1, N2, w, valid, a.hs, a.P);
         if (active) {
             for (int p = 0; p < 32; ++p)
-                if ((valid >> p) & 1u) dst[32 * (int64_t)w + p] = ((up >> p) & 1u) ? 1 : -1;
+                if ((valid >> p) & 1u)
+                    *checked(dst, 32 * (uint64_t)w + p, (uint64_t)a.N, SHK_SITE) = ((up >> p) & 1u) ? 1 : -1;
         }
         accumulate_step<HALF>(acc, up, S, N1, N2, valid, cnn);
     }
@@ -689,17 +694,18 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs a) {
         const uint32_t valid = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
         bits &= valid;
         if (LAYOUT == kBitpack) {
-            static_cast<uint32_t*>(a.plane)[w] = bits;
+            *checked(static_cast<uint32_t*>(a.plane), w, a.nblocks, SHK_SITE) = bits;
         } else if (valid == 0xffffffffu && ((a.L & 31u) == 0u)) {
             uint4 lo, hi;
             unpack32(bits, lo, hi);
-            uint4* d4 = reinterpret_cast<uint4*>(static_cast<int8_t*>(a.plane) + 32 * (size_t)w);
-            d4[0] = lo;
-            d4[1] = hi;
+            uint4* q4 = reinterpret_cast<uint4*>(a.plane);
+            *checked(q4, 2 * (uint64_t)w, 2 * (uint64_t)a.nblocks, SHK_SITE) = lo;
+            *checked(q4, 2 * (uint64_t)w + 1, 2 * (uint64_t)a.nblocks, SHK_SITE) = hi;
         } else {
             int8_t* d = static_cast<int8_t*>(a.plane);
             for (int p = 0; p < 32; ++p)
-                if ((valid >> p) & 1u) d[32 * (int64_t)w + p] = ((bits >> p) & 1u) ? 1 : -1;
+                if ((valid >> p) & 1u)
+                    *checked(d, 32 * (uint64_t)w + p, (uint64_t)a.N, SHK_SITE) = ((bits >> p) & 1u) ? 1 : -1;
         }
     }
 }
@@ -752,16 +758,16 @@ __global__ void __launch_bounds__(1024) k_run_small(const SmallArgs a) {
         uint32_t bs = 0, bt = 0;
         if (w < a.nblocks) {
             if (LAYOUT == kBitpack) {
-                bs = static_cast<const uint32_t*>(a.sigma)[w];
-                bt = static_cast<const uint32_t*>(a.tau)[w];
+                bs = *checked(static_cast<const uint32_t*>(a.sigma), w, a.nblocks, SHK_SITE);
+                bt = *checked(static_cast<const uint32_t*>(a.tau), w, a.nblocks, SHK_SITE);
             } else {
                 const int8_t* s8 = static_cast<const int8_t*>(a.sigma);
                 const int8_t* t8 = static_cast<const int8_t*>(a.tau);
                 for (int p = 0; p < 32; ++p) {
                     const int64_t u = 32 * (int64_t)w + p;
                     if (u >= a.N) break;
-                    bs |= (uint32_t)(s8[u] > 0) << p;
-                    bt |= (uint32_t)(t8[u] > 0) << p;
+                    bs |= (uint32_t)(*checked(s8, (uint64_t)u, (uint64_t)a.N, SHK_SITE) > 0) << p;
+                    bt |= (uint32_t)(*checked(t8, (uint64_t)u, (uint64_t)a.N, SHK_SITE) > 0) << p;
                 }
             }
         }
@@ -826,16 +832,16 @@ __global__ void __launch_bounds__(1024) k_run_small(const SmallArgs a) {
     // store both planes back
     for (uint32_t w = threadIdx.x; w < a.nblocks; w += blockDim.x) {
         if (LAYOUT == kBitpack) {
-            static_cast<uint32_t*>(a.sigma)[w] = sg[w];
-            static_cast<uint32_t*>(a.tau)[w] = tu[w];
+            *checked(static_cast<uint32_t*>(a.sigma), w, a.nblocks, SHK_SITE) = sg[w];
+            *checked(static_cast<uint32_t*>(a.tau), w, a.nblocks, SHK_SITE) = tu[w];
         } else {
             int8_t* s8 = static_cast<int8_t*>(a.sigma);
             int8_t* t8 = static_cast<int8_t*>(a.tau);
             for (int p = 0; p < 32; ++p) {
                 const int64_t u = 32 * (int64_t)w + p;
                 if (u >= a.N) break;
-                s8[u] = ((sg[w] >> p) & 1u) ? 1 : -1;
-                t8[u] = ((tu[w] >> p) & 1u) ? 1 : -1;
+                *checked(s8, (uint64_t)u, (uint64_t)a.N, SHK_SITE) = ((sg[w] >> p) & 1u) ? 1 : -1;
+                *checked(t8, (uint64_t)u, (uint64_t)a.N, SHK_SITE) = ((tu[w] >> p) & 1u) ? 1 : -1;
             }
         }
     }
@@ -1063,5 +1069,7 @@ cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const Dr
     }
     return cudaGetLastError();
 }
+
+unsigned bounds_site_kernels() { return take_bounds_site(); }
 
 }  // namespace shk

@@ -11,6 +11,7 @@
 // own (device.cuh).
 #include <algorithm>
 
+#define SHK_TU_ID 3
 #include "internal.h"
 #include "sweep.cuh"
 
@@ -35,9 +36,9 @@ __device__ __forceinline__ uint32_t shifted_row_word(const uint32_t* row, uint32
     uint32_t cw = c + (l >> 5);     // c < Wr and l < L, so below 2 Wr
     if (cw >= Wr) cw -= Wr;
     const uint32_t sh = l & 31u;
-    const uint32_t lo = row[cw];
+    const uint32_t lo = *checked(row, cw, Wr, SHK_SITE);
     if (sh == 0) return lo;
-    const uint32_t hi = row[cw + 1 == Wr ? 0 : cw + 1];
+    const uint32_t hi = *checked(row, cw + 1 == Wr ? 0 : cw + 1, Wr, SHK_SITE);
     return (lo >> sh) | (hi << (32u - sh));
 }
 
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_diag_corr(const CorrArgs a) {
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
         const uint32_t j = fdiv(w, a.div_row), c = w - j * a.Wr;
-        const uint32_t s = a.plane[w];
+        const uint32_t s = *checked(a.plane, w, a.nblocks, SHK_SITE);
 #pragma unroll
         for (int k = 0; k < kMaxLags; ++k) {
             if (k < a.n_lags) {
@@ -134,18 +135,18 @@ __device__ __forceinline__ CbWord cb_word(const uint32_t* pl, uint32_t w, uint32
                                           uint32_t Wr, uint32_t nblocks, uint32_t parity) {
     CbWord r;
     r.o = (row + parity) & 1u;
-    const uint32_t S = pl[w];
-    const uint32_t U = pl[row + 1 < L ? w + Wr : w + Wr - nblocks];
-    const uint32_t D = pl[row > 0 ? w - Wr : w + nblocks - Wr];
+    const uint32_t S = *checked(pl, w, nblocks, SHK_SITE);
+    const uint32_t U = *checked(pl, row + 1 < L ? w + Wr : w + Wr - nblocks, nblocks, SHK_SITE);
+    const uint32_t D = *checked(pl, row > 0 ? w - Wr : w + nblocks - Wr, nblocks, SHK_SITE);
     r.U = even_bits(U >> r.o);
     r.D = even_bits(D >> r.o);
     if (r.o == 0) {   // active at even positions: left and right neighbours are the odd bits
-        const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
+        const uint32_t prev = *checked(pl, col > 0 ? w - 1 : w + Wr - 1, nblocks, SHK_SITE);
         const uint32_t odd = even_bits(S >> 1);
         r.Rt = odd;
         r.Lf = ((odd << 1) | (prev >> 31)) & 0xFFFFu;
     } else {          // active at odd positions: neighbours are the even bits
-        const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
+        const uint32_t next = *checked(pl, col + 1 < Wr ? w + 1 : w + 1 - Wr, nblocks, SHK_SITE);
         const uint32_t even = even_bits(S);
         r.Lf = even;
         r.Rt = (even >> 1) | ((next & 1u) << 15);
@@ -187,13 +188,15 @@ __device__ __forceinline__ CbBlock cb_block(const uint32_t* pl, uint32_t d, uint
 
 // Writes the 32 drawn spins of draw block d back into plane words 2d, 2d + 1
 // (their other bits are unchanged); returns the new words.
-__device__ __forceinline__ uint2 cb_store(uint32_t* pl, uint32_t d, uint32_t up, uint32_t o0, uint32_t o1) {
-    const uint32_t w0 = 2 * d;
+__device__ __forceinline__ uint2 cb_store(uint32_t* pl, uint32_t d, uint32_t up, uint32_t o0, uint32_t o1,
+                                          uint32_t nblocks) {
+    uint32_t* p0 = checked(pl, 2 * (uint64_t)d, nblocks, SHK_SITE);
+    uint32_t* p1 = checked(pl, 2 * (uint64_t)d + 1, nblocks, SHK_SITE);
     const uint32_t m0 = 0x55555555u << o0, m1 = 0x55555555u << o1;
-    const uint32_t v0 = (pl[w0] & ~m0) | (spread_even(up) << o0);
-    const uint32_t v1 = (pl[w0 + 1] & ~m1) | (spread_even(up >> 16) << o1);
-    pl[w0] = v0;
-    pl[w0 + 1] = v1;
+    const uint32_t v0 = (*p0 & ~m0) | (spread_even(up) << o0);
+    const uint32_t v1 = (*p1 & ~m1) | (spread_even(up >> 16) << o1);
+    *p0 = v0;
+    *p1 = v1;
     return make_uint2(v0, v1);
 }
 
@@ -211,7 +214,7 @@ __device__ __forceinline__ void cb_accumulate(int (&acc)[2], uint2 v, uint32_t u
 template <int PARITY>
 __device__ __forceinline__ void cb_finish(const SweepArgs& a, uint32_t* pl, uint32_t d, uint32_t up, uint32_t o0,
                                           uint32_t o1, int (&acc)[2], const CbBlock* known) {
-    const uint2 v = cb_store(pl, d, up, o0, o1);
+    const uint2 v = cb_store(pl, d, up, o0, o1, a.nblocks);
     if (PARITY == 1 && a.obs_cur != nullptr) {
         if (known != nullptr) {
             cb_accumulate(acc, v, up, known->U, known->D, known->Lf, known->Rt);
@@ -441,8 +444,8 @@ __device__ __forceinline__ void pair_step(const PairPlanes& p, unsigned long lon
                 uint32_t up[2];
                 draw_coupled(k, d, in ? 0xffffffffu : 0u, hs + (uint32_t)half, P, up);
                 if (in) {
-                    cb_store(p.st, d, up[0], c0.o0, c0.o1);
-                    cb_store(p.sb, d, up[1], c0.o0, c0.o1);
+                    cb_store(p.st, d, up[0], c0.o0, c0.o1, p.nb);
+                    cb_store(p.sb, d, up[1], c0.o0, c0.o1, p.nb);
                 }
             }
         }
@@ -605,5 +608,7 @@ cudaError_t launch_checkerboard(const Geometry& g, void* plane, const DrawParams
     }
     return cudaGetLastError();
 }
+
+unsigned bounds_site_sampling() { return take_bounds_site(); }
 
 }  // namespace shk

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "bounds.cuh"
 
 namespace shk {
 
@@ -35,20 +36,21 @@ __device__ __forceinline__ void words_aligned(const uint32_t* __restrict__ pl, u
                                               uint32_t row, uint32_t col, uint32_t L, uint32_t Wr,
                                               uint32_t nblocks, uint32_t& S, uint32_t& N1,
                                               uint32_t& N2) {
-    S = pl[w];
+    S = *checked(pl, w, nblocks, SHK_SITE);
     if (HALF == 0) {
-        N1 = pl[row > 0 ? w - Wr : w + nblocks - Wr];
-        const uint32_t prev = pl[col > 0 ? w - 1 : w + Wr - 1];
+        N1 = *checked(pl, row > 0 ? w - Wr : w + nblocks - Wr, nblocks, SHK_SITE);
+        const uint32_t prev = *checked(pl, col > 0 ? w - 1 : w + Wr - 1, nblocks, SHK_SITE);
         N2 = (S << 1) | (prev >> 31);
     } else {
-        N1 = pl[row + 1 < L ? w + Wr : w + Wr - nblocks];
-        const uint32_t next = pl[col + 1 < Wr ? w + 1 : w + 1 - Wr];
+        N1 = *checked(pl, row + 1 < L ? w + Wr : w + Wr - nblocks, nblocks, SHK_SITE);
+        const uint32_t next = *checked(pl, col + 1 < Wr ? w + 1 : w + 1 - Wr, nblocks, SHK_SITE);
         N2 = (S >> 1) | (next << 31);
     }
 }
 
-__device__ __forceinline__ uint32_t bit_of(const uint32_t* pl, int64_t v) {
-    return (pl[v >> 5] >> (v & 31)) & 1u;
+// Bit of site v of a bit plane of N sites.
+__device__ __forceinline__ uint32_t bit_of(const uint32_t* pl, int64_t v, int64_t N) {
+    return (*checked(pl, (uint64_t)(v >> 5), (uint64_t)((N + 31) >> 5), SHK_SITE) >> (v & 31)) & 1u;
 }
 
 // Generic side length (L % 32 != 0): site-by-site neighbour bits of block w of
@@ -70,9 +72,9 @@ __device__ __forceinline__ void words_generic(const uint32_t* pl, uint32_t w, in
             a = j + 1 < L ? u + L : u + L - N;
             b = i + 1 < L ? u + 1 : u + 1 - L;
         }
-        S |= bit_of(pl, u) << p;
-        N1 |= bit_of(pl, a) << p;
-        N2 |= bit_of(pl, b) << p;
+        S |= bit_of(pl, u, N) << p;
+        N1 |= bit_of(pl, a, N) << p;
+        N2 |= bit_of(pl, b, N) << p;
         valid |= 1u << p;
     }
 }
@@ -95,9 +97,9 @@ __device__ __forceinline__ void bytes_generic(const int8_t* __restrict__ pl, uin
             a = j + 1 < L ? u + L : u + L - N;
             b = i + 1 < L ? u + 1 : u + 1 - L;
         }
-        S |= (uint32_t)(pl[u] > 0) << p;
-        N1 |= (uint32_t)(pl[a] > 0) << p;
-        N2 |= (uint32_t)(pl[b] > 0) << p;
+        S |= (uint32_t)(*checked(pl, (uint64_t)u, (uint64_t)N, SHK_SITE) > 0) << p;
+        N1 |= (uint32_t)(*checked(pl, (uint64_t)a, (uint64_t)N, SHK_SITE) > 0) << p;
+        N2 |= (uint32_t)(*checked(pl, (uint64_t)b, (uint64_t)N, SHK_SITE) > 0) << p;
         valid |= 1u << p;
     }
 }
@@ -108,19 +110,21 @@ __device__ __forceinline__ void bytes_aligned(const int8_t* __restrict__ pl, uin
                                               uint32_t col, uint32_t L, uint32_t Wr,
                                               uint32_t nblocks, uint32_t& S, uint32_t& N1,
                                               uint32_t& N2) {
-    const uint4* s4 = reinterpret_cast<const uint4*>(pl + 32 * (size_t)w);
-    S = pack_up32(__ldg(s4), __ldg(s4 + 1));
+    const uint4* q4 = reinterpret_cast<const uint4*>(pl);     // 16-byte chunks, two per block
+    const uint64_t n4 = 2 * (uint64_t)nblocks, nbytes = 32 * (uint64_t)nblocks;
+    S = pack_up32(__ldg(checked(q4, 2 * (uint64_t)w, n4, SHK_SITE)),
+                  __ldg(checked(q4, 2 * (uint64_t)w + 1, n4, SHK_SITE)));
     uint32_t wn;
     if (HALF == 0) wn = row > 0 ? w - Wr : w + nblocks - Wr;
     else wn = row + 1 < L ? w + Wr : w + Wr - nblocks;
-    const uint4* n4 = reinterpret_cast<const uint4*>(pl + 32 * (size_t)wn);
-    N1 = pack_up32(__ldg(n4), __ldg(n4 + 1));
+    N1 = pack_up32(__ldg(checked(q4, 2 * (uint64_t)wn, n4, SHK_SITE)),
+                   __ldg(checked(q4, 2 * (uint64_t)wn + 1, n4, SHK_SITE)));
     if (HALF == 0) {
         const size_t idx = col > 0 ? 32 * (size_t)w - 1 : 32 * (size_t)w + L - 1;
-        N2 = (S << 1) | (uint32_t)(__ldg(pl + idx) > 0);
+        N2 = (S << 1) | (uint32_t)(__ldg(checked(pl, idx, nbytes, SHK_SITE)) > 0);
     } else {
         const size_t idx = col + 1 < Wr ? 32 * (size_t)w + 32 : 32 * (size_t)w + 32 - L;
-        N2 = (S >> 1) | ((uint32_t)(__ldg(pl + idx) > 0) << 31);
+        N2 = (S >> 1) | ((uint32_t)(__ldg(checked(pl, idx, nbytes, SHK_SITE)) > 0) << 31);
     }
 }
 

@@ -144,3 +144,17 @@ def test_philox_peak_argument_checks_without_gpu():
     assert so.shk_philox_peak(0, 4, ctypes.c_void_p(16), None) == _lib.EINVAL
     assert so.shk_philox_peak(4, 0, ctypes.c_void_p(16), None) == _lib.EINVAL
     assert so.shk_philox_peak(4, 4, None, None) == _lib.EINVAL
+
+
+def test_debug_bounds_is_refused_by_the_normal_build():
+    so = _lib.lib()
+    site = np.ones(1, dtype=np.uint32)
+    assert so.shk_debug_bounds(site.ctypes.data) == _lib.ESTATE and site[0] == 0
+
+
+def test_bounds_checked_build_exports_the_same_symbols():
+    from paper_1908_07341_gb300 import build
+    path = build.build(debug_bounds=True)
+    dbg = ctypes.CDLL(path)
+    for name in _lib.SIGNATURES:
+        assert hasattr(dbg, name), name
