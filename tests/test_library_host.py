@@ -158,3 +158,32 @@ def test_bounds_checked_build_exports_the_same_symbols():
     dbg = ctypes.CDLL(path)
     for name in _lib.SIGNATURES:
         assert hasattr(dbg, name), name
+
+
+def test_coalescence_and_cftp_argument_checks_without_gpu():
+    so = _lib.lib()
+    dummy = ctypes.c_void_p(256)
+    L = np.array([32, 48], dtype=np.int32)
+    q = np.array([1.0, 1.0])
+    J = np.array([0.3, 0.3])
+    seed = np.array([1, 1], dtype=np.uint64)
+    ids = np.array([0, 1], dtype=np.uint32)
+    T = np.zeros(2, dtype=np.uint64)
+    ks = np.zeros(2, dtype=np.int32)
+    nb = so.shk_coalescence_scratch_bytes(2)
+    args = (L.ctypes.data, q.ctypes.data, J.ctypes.data, seed.ctypes.data, ids.ctypes.data)
+    # L = 48 is not a multiple of 32; unknown dynamics; steps out of range
+    assert so.shk_coalescence_times(0, 2, *args, 100, dummy, nb, T.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_coalescence_times(7, 1, *args, 100, dummy, nb, T.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_coalescence_times(0, 1, *args, 0, dummy, nb, T.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_coalescence_times(0, 1, *args, 100, dummy, 8, T.ctypes.data, None) == _lib.ENOMEM
+    nc = so.shk_cftp_scratch_bytes(2)
+    assert so.shk_cftp(0, 1, *args, 21, dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL  # k_max
+    assert so.shk_cftp(0, 2, *args, 10, dummy, 288, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL  # L = 48
+    assert so.shk_cftp(0, 1, *args, 10, dummy, 100, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL  # stride < L^2/8
+    assert so.shk_cftp(0, 1, *args, 10, dummy, 128, dummy, 4, ks.ctypes.data, None) == _lib.ENOMEM
+    # the checkerboard dynamics needs no q
+    assert so.shk_cftp(1, 1, L.ctypes.data, None, J.ctypes.data, seed.ctypes.data, ids.ctypes.data, 21,
+                       dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL       # still k_max
+    assert so.shk_cftp(0, 1, L.ctypes.data, None, J.ctypes.data, seed.ctypes.data, ids.ctypes.data, 10,
+                       dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL       # shaken needs q
