@@ -702,3 +702,23 @@ def test_cftp_checkerboard_4x4_magnetisation_energy_law(orc):
     assert np.all(ks >= 0)
     counts = np.bincount(inv[codes.astype(np.int64)], minlength=keys.size)
     assert _chi2_pvalue(counts, probs) > 1e-4
+
+
+def test_exact_diagonal_correlations_order_theorem_2_4(orc):
+    """Section 3.3 (Theorem 2.4 of the cited work): under the stationary law
+    pi_s the SW-NE correlation E[s_(0,0) s_(1,1)] lies below the NW-SE one
+    E[s_(0,1) s_(1,0)] for small q, and the two meet as q grows.  Checked on
+    the exact closed-form law of the 4x4 torus (65536 states), with the
+    per-state sums taken from the oracle's diagonal-correlation routine."""
+    L, N = 4, 16
+    S = exact.spin_table(N)
+    sums = np.array([orc.diag_correlations(S[c].astype(np.int8), L, [1]) for c in range(2 ** N)],
+                    dtype=np.float64) / N        # columns: SW-NE, NW-SE
+    gaps = []
+    for q in (0.05, 0.2, 0.5, 1.0, 2.0, 3.0):
+        pi = exact.pi_s_closed_form(L, q, 0.7)
+        swne, nwse = pi @ sums[:, 0], pi @ sums[:, 1]
+        gaps.append(nwse - swne)
+    assert gaps[0] > 0.3 and all(g > 0 for g in gaps), gaps
+    assert all(a > b for a, b in zip(gaps, gaps[1:])), gaps    # the gap closes as q grows
+    assert gaps[-1] < 1e-2
