@@ -236,7 +236,7 @@ def _oracle_rate_all_cores(steps: int, warmup: int = 0):
             sigma[sl] = rng.integers(0, 2, size=1024 * L, dtype=np.int8) * 2 - 1
         del sigma
         ctx = mp.get_context("spawn")
-        barrier = ctx.Barrier(cores)
+        barrier = ctx.Barrier(cores, timeout=600)   # a worker that dies breaks it for the others
         results = ctx.Queue()
         bands = [(L * k // cores, L * (k + 1) // cores) for k in range(cores)]
         procs = [ctx.Process(target=_oracle_band_worker,
@@ -244,7 +244,14 @@ def _oracle_rate_all_cores(steps: int, warmup: int = 0):
                  for r0, r1 in bands]
         for p in procs:
             p.start()
-        times = [results.get(timeout=3600) for _ in procs]
+        import queue
+        times = []
+        while len(times) < cores:
+            try:
+                times.append(results.get(timeout=5))
+            except queue.Empty:
+                if not any(p.is_alive() for p in procs) and results.empty():
+                    raise RuntimeError("an oracle worker process failed")
         for p in procs:
             p.join()
         dt = max(times)
