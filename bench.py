@@ -455,6 +455,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         line["serving"] = bench_serving(dev, stream, n_jobs=args.serving_jobs)
     if not args.no_section3:
         line["section3"] = bench_section3(dev, stream)
+        line["l_sweep"] = bench_l_sweep(dev, stream)
     if world == 1 and not args.no_cpu_baseline:
         rate, secs, units, cores = _oracle_rate_all_cores(steps=4, warmup=1)
         line["cpu_baseline"] = {
@@ -583,6 +584,36 @@ def bench_section3(dev, stream) -> dict:
                    "ms": ms, "samples_per_s": float((ks >= 0).sum()) / (ms / 1e3),
                    "value": steps * 4 * L * L / (ms / 1e3), "unit": UNIT + " (both chains, all attempts)"}
     return out
+
+
+def bench_l_sweep(dev, stream) -> dict:
+    """The paper's own benchmark shape (Section 4, time per update against L):
+    J = 0.44, q = 0.66, one bit-packed lattice of side L = 32 .. 16384 (powers
+    of two), random start; time per full step through shk_run, timed with
+    events on `stream` over enough steps to last a few milliseconds."""
+    import torch
+
+    import paper_1908_07341_gb300 as shk
+
+    rows = []
+    for e in range(5, 15):
+        side = 1 << e
+        n = int(max(20, min(4000, (1 << 29) // (side * side))))
+        lat = shk.Lattice(side, "bitpack", device=dev, stream=stream).set_seed(SEED, 0).set_params(0.66, 0.44)
+        lat.init("random", init_seed=INIT_SEED)
+        lat.run(min(n, 50))
+        s_ev = torch.cuda.Event(enable_timing=True)
+        e_ev = torch.cuda.Event(enable_timing=True)
+        s_ev.record(stream)
+        lat.run(n)
+        e_ev.record(stream)
+        torch.cuda.synchronize()
+        ms = s_ev.elapsed_time(e_ev)
+        rows.append({"L": side, "steps": n, "us_per_step": 1e3 * ms / n,
+                     "site_updates_per_s": 2.0 * side * side * n / (ms / 1e3)})
+        lat.close()
+    return {"workload": "one L x L bit-packed torus, J=0.44, q=0.66, random start, full steps through shk_run "
+                        "with per-step sums", "rows": rows}
 
 
 def bench_serving(dev, stream, n_jobs: int = 200, steps_per_launch: int = 2, launches_per_tick: int = 16):
