@@ -613,7 +613,7 @@ def bench_l_sweep(dev, stream) -> dict:
                      "site_updates_per_s": 2.0 * side * side * n / (ms / 1e3)})
         lat.close()
     return {"workload": "one L x L bit-packed torus, J=0.44, q=0.66, random start, full steps through shk_run "
-                        "with per-step sums", "rows": rows}
+                        "(sums of the last step kept on the device)", "rows": rows}
 
 
 def bench_serving(dev, stream, n_jobs: int = 200, steps_per_launch: int = 2, launches_per_tick: int = 16):
