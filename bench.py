@@ -609,9 +609,26 @@ def bench_l_sweep(dev, stream) -> dict:
         e_ev.record(stream)
         torch.cuda.synchronize()
         ms = s_ev.elapsed_time(e_ev)
-        rows.append({"L": side, "steps": n, "us_per_step": 1e3 * ms / n,
-                     "site_updates_per_s": 2.0 * side * side * n / (ms / 1e3)})
+        row = {"L": side, "steps": n, "us_per_step": 1e3 * ms / n,
+               "site_updates_per_s": 2.0 * side * side * n / (ms / 1e3)}
         lat.close()
+        if side <= 4096:
+            # the same lattice as a batch of one: k steps per launch of the
+            # persistent kernel, one graph node replayed
+            from paper_1908_07341_gb300.batch import Batch
+            k = 8 if side <= 512 else 2        # deeper temporal blocking only while halos are cheap
+            nb = max(k, (n // k) * k)
+            b = Batch([side], [0.66], [0.44], [SEED], [0], device=dev, stream=stream)
+            b.configure(k, 256, 1 << 17).init("random", INIT_SEED)
+            b.run(k)
+            s_ev.record(stream)
+            b.run(nb)
+            e_ev.record(stream)
+            torch.cuda.synchronize()
+            ms_b = s_ev.elapsed_time(e_ev)
+            row["batch_of_one_us_per_step"] = 1e3 * ms_b / nb
+            b.close()
+        rows.append(row)
     return {"workload": "one L x L bit-packed torus, J=0.44, q=0.66, random start, full steps through shk_run "
                         "(sums of the last step kept on the device)", "rows": rows}
 
