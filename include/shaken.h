@@ -244,6 +244,22 @@ int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const dou
  * the measured Philox ceiling of the bit-packed draw.  Asynchronous. */
 int shk_philox_peak(int blocks, uint32_t iters, uint32_t* dev_out, void* stream);
 
+/* The one-launch path of shk_run: with it enabled, a bit-packed lattice with
+ * L^2 > 65536 and L <= 4096 runs all n steps in a single cooperative launch, a bounded grid
+ * barrier between the half-steps (same spins and sums as the per-launch
+ * path).  If a barrier gives up (it polls at most about two seconds), the
+ * next shk_read_observables / shk_read_spins on the handle returns
+ * SHK_ETIMEOUT.  shk_set_one_launch(1) enables the path, process-wide; it is
+ * off by default because on a GB300 it measured no faster than the
+ * per-launch path (both 8 to 20 us per step for L = 288 .. 4096), while it
+ * issues one launch per run instead of 2n + 1 (less host work).
+ * shk_barrier_timeout_test launches the barrier with an arrival count that
+ * can never complete and reports in *timed_out whether both waiting CTAs gave
+ * up after spin_limit polls (1..2^20); dev_words: 3 device uint32.
+ * Synchronous.  It exists to test the failure path without a fault. */
+int shk_set_one_launch(int enabled);
+int shk_barrier_timeout_test(unsigned int spin_limit, uint32_t* dev_words, int* timed_out, void* stream);
+
 /* ------------------------------------------------------------ lattice handle */
 
 typedef struct shk_lattice shk_lattice;

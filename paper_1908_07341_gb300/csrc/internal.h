@@ -92,11 +92,20 @@ int sm_count();
 // Message returned by shk_last_error(NULL) on this host thread.
 void set_thread_error(const char* msg);
 
+// One cooperative launch for a whole run of a mid-size bit-packed lattice
+// (coop.cu); bar: 3 zeroed device words (arrivals, generation, timeout flag).
+bool coop_path_fits(const Geometry& g);
+cudaError_t launch_run_coop(const Geometry& g, void* sigma, void* tau, const DrawParams& P, uint64_t t0,
+                            uint64_t n, long long* obs, long long* ring, unsigned int* bar,
+                            unsigned int spin_limit, cudaStream_t st);
+cudaError_t launch_barrier_probe(unsigned int* bar, unsigned int spin_limit, cudaStream_t st);
+
 // First bounds-check failure site recorded by each translation unit in the
 // debug build (0 = none; always 0 in the normal build), cleared on read.
 unsigned bounds_site_kernels();
 unsigned bounds_site_batch();
 unsigned bounds_site_sampling();
+unsigned bounds_site_coop();
 
 // Named range on the host timeline for profilers that record NVTX (no-op
 // when no tool is attached).

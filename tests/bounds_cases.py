@@ -37,6 +37,16 @@ def main() -> int:
         assert np.array_equal(lat.read_spins(0).reshape(-1), s), (L, layout)
         lat.close()
         checked.append(f"run {layout} L={L}")
+    # the one-launch (cooperative) path
+    so.shk_set_one_launch(1)
+    lat = shk.Lattice(512, "bitpack").set_seed(5, 1).set_params(0.8, 0.4).init("random", init_seed=3)
+    obs = lat.run(3, obs=True).cpu().numpy()
+    s = orc.init_plane(512, orc.INIT_RANDOM, 3, 1, 0)
+    t = orc.init_plane(512, orc.INIT_RANDOM, 3, 1, 1)
+    assert np.array_equal(obs, orc.run(s, t, 512, 0.8, 0.4, 5, 1, 0, 3))
+    lat.close()
+    so.shk_set_one_launch(0)
+    checked.append("one-launch run")
     # every launch shape of the sweeps at a strip-walk size
     from paper_1908_07341_gb300 import tune
     for layout in ("bitpack", "int8"):

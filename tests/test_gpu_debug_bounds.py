@@ -25,4 +25,4 @@ def test_bounds_checked_build_records_no_out_of_range_access():
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
     assert out["status"] == 0 and out["site"] == 0, out
-    assert len(out["checked"]) == 12
+    assert len(out["checked"]) == 13

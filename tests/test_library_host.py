@@ -72,7 +72,7 @@ def test_bad_arguments_are_rejected_without_a_gpu(so):
     assert so.shk_plane_bytes(_lib.MAX_L * 2, _lib.INT8) == 0
     assert so.shk_plane_bytes(64, 7) == 0
     assert so.shk_plane_bytes(64, _lib.BITPACK) == 512
-    assert so.shk_lattice_bytes(16384, _lib.BITPACK) == 2 * 16384 * 16384 // 8 + 256
+    assert so.shk_lattice_bytes(16384, _lib.BITPACK) == 2 * 16384 * 16384 // 8 + 512   # planes, ring, barrier
     h = ctypes.c_void_p()
     assert so.shk_lattice_create(33, _lib.BITPACK, 256, 1 << 20, None, ctypes.byref(h)) == _lib.EINVAL
     assert so.shk_lattice_create(64, _lib.BITPACK, 0, 1 << 20, None, ctypes.byref(h)) == _lib.EINVAL
@@ -187,3 +187,12 @@ def test_coalescence_and_cftp_argument_checks_without_gpu():
                        dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL       # still k_max
     assert so.shk_cftp(0, 1, L.ctypes.data, None, J.ctypes.data, seed.ctypes.data, ids.ctypes.data, 10,
                        dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL       # shaken needs q
+
+
+def test_barrier_timeout_test_argument_checks_without_gpu():
+    so = _lib.lib()
+    flag = np.zeros(1, dtype=np.int32)
+    assert so.shk_barrier_timeout_test(0, ctypes.c_void_p(256), flag.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_barrier_timeout_test(1 << 21, ctypes.c_void_p(256), flag.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_barrier_timeout_test(10, None, flag.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_set_one_launch(0) == _lib.OK
