@@ -280,7 +280,8 @@ int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t l
     if (!make_geometry(L, kBitpack, &g))
         return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
     if (plane == nullptr) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: plane is NULL");
-    if (t0 + n_steps > SHK_MAX_STEP) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: step index would exceed 2^31");
+    if (t0 > SHK_MAX_STEP || n_steps > SHK_MAX_STEP - t0)
+        return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: step index would exceed 2^31");
     DrawParams P;
     if (!checkerboard_draw_params(J, seed, lattice_id, &P))
         return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: J must be finite");
@@ -500,7 +501,7 @@ int shk_run(shk_lattice* lat, uint64_t n_steps, int64_t* dev_obs) {
     if (lat == nullptr) return fail(nullptr, SHK_EINVAL, "shk_run: NULL handle");
     if (!lat->params_set) return fail(lat, SHK_ESTATE, "shk_run: call shk_set_params first");
     if (n_steps == 0) return SHK_OK;
-    if (lat->step + n_steps > SHK_MAX_STEP)
+    if (n_steps > SHK_MAX_STEP - lat->step)
         return fail(lat, SHK_EINVAL, "shk_run: step counter would exceed 2^31");
     DrawParams P;
     make_draw_params(lat->seed, lat->lattice_id, lat->T, 0u, &P);

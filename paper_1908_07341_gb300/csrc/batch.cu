@@ -648,7 +648,7 @@ int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
     const TraceRange trace("shk_batch_run");
     if (!b) return bfail(nullptr, SHK_EINVAL, "shk_batch_run: NULL handle");
     if (n_steps == 0) return SHK_OK;
-    if (b->step + n_steps > SHK_MAX_STEP)
+    if (b->step > SHK_MAX_STEP || n_steps > SHK_MAX_STEP - b->step)
         return bfail(b, SHK_EINVAL, "shk_batch_run: step counter would exceed 2^31");
     if (n_steps % (uint64_t)b->k != 0)
         return bfail(b, SHK_EINVAL, "shk_batch_run: n_steps=%llu is not a multiple of steps_per_launch=%d",

@@ -69,7 +69,7 @@ extern "C" int shk_shaken_run_static(int layout, void* sigma, int L, double q, d
                     "shk_shaken_run_static: lattice too large for the static scratch "
                     "(at most 8 MiB per plane: bit-packed L <= 8192, int8 L <= 2896)");
     if (sigma == nullptr) return fail(SHK_EINVAL, "shk_shaken_run_static: sigma is NULL");
-    if (t0 + n_steps > SHK_MAX_STEP)
+    if (t0 > SHK_MAX_STEP || n_steps > SHK_MAX_STEP - t0)
         return fail(SHK_EINVAL, "shk_shaken_run_static: step index would exceed 2^31");
     uint32_t T[6];
     if (host_thresholds(q, J, T) != SHK_OK)

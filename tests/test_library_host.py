@@ -196,3 +196,10 @@ def test_barrier_timeout_test_argument_checks_without_gpu():
     assert so.shk_barrier_timeout_test(1 << 21, ctypes.c_void_p(256), flag.ctypes.data, None) == _lib.EINVAL
     assert so.shk_barrier_timeout_test(10, None, flag.ctypes.data, None) == _lib.EINVAL
     assert so.shk_set_one_launch(0) == _lib.OK
+
+
+def test_step_counters_do_not_wrap():
+    so = _lib.lib()
+    huge = 2 ** 64 - 5
+    assert so.shk_checkerboard_run(ctypes.c_void_p(256), 64, 0.4, 1, 0, 3, huge, None, None) == _lib.EINVAL
+    assert so.shk_checkerboard_run(ctypes.c_void_p(256), 64, 0.4, 1, 0, huge, 3, None, None) == _lib.EINVAL
