@@ -750,7 +750,7 @@ def _kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("device.cuh", "sweep.cuh", "kernels.cu", "batch.cu"):
+    for f in ("device.cuh", "bounds.cuh", "sweep.cuh", "kernels.cu"):     # the sweep kernels' sources
         with open(os.path.join(ROOT, "paper_1908_07341_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
