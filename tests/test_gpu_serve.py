@@ -160,3 +160,39 @@ def test_result_log_lines(tmp_path):
     for r in lines:
         want = next(g for g in got if g["job_id"] == r["job_id"])
         assert r["stats"] == want["stats"].tolist() and r["sigma_hash"] == want["sigma_hash"]
+
+
+def test_serving_stream_jobs_spot_checked_against_the_oracle(orc):
+    """Jobs of the serving workload itself (the first 300 jobs of the Poisson
+    stream, L log-uniform in [64, 4096], steps log-uniform in [10^3, 10^5]) in
+    the benchmark's launch shape (2 steps per launch, 16 launches per tick,
+    256 threads, 2^18-site tiles), all in one mix; the smallest ones (the
+    oracle finishes them in seconds) are recomputed by the oracle: exact
+    statistics after burn-in, last-step sums and the hash of the final sigma."""
+    from paper_1908_07341_gb300 import workloads
+    from paper_1908_07341_gb300.lattice import pack_bits
+    w = workloads.serving_stream(n_jobs=300)
+    jobs = w["jobs"]
+    cost = [j["L"] ** 2 * j["n_steps"] for j in jobs]
+    check = sorted(range(len(jobs)), key=lambda i: cost[i])[:4]
+    mix = sorted(set(check) | set(range(0, 300, 30)))        # the checked jobs among larger ones
+    srv = Server(max_slots=64, arena_bytes=1 << 30).configure(steps_per_launch=2, launches_per_tick=16,
+                                                              block_threads=256, tile_sites=1 << 18)
+    ids = {srv.submit(**jobs[i]): i for i in mix}
+    got = {}
+    for _ in range(100_000):
+        srv.tick()
+        got.update({ids[r["job_id"]]: r for r in srv.poll()})
+        if len(got) == len(mix):
+            break
+    assert len(got) == len(mix)
+    for i in check:
+        j = jobs[i]
+        L = j["L"]
+        s = orc.init_plane(L, orc.INIT_RANDOM, j["init_seed"], j["lattice_id"], 0)
+        t = orc.init_plane(L, orc.INIT_RANDOM, j["init_seed"], j["lattice_id"], 1)
+        obs = orc.run(s, t, L, j["q"], j["J"], j["seed"], j["lattice_id"], 0, j["n_steps"])
+        assert got[i]["status"] == 0 and got[i]["steps_done"] == j["n_steps"]
+        assert np.array_equal(got[i]["stats"], stats_from_observables(obs[j["burn_in"]:])), i
+        assert np.array_equal(got[i]["last_obs"], obs[-1]), i
+        assert got[i]["sigma_hash"] == fnv1a64(pack_bits(s).view(np.uint8).tobytes()), i
