@@ -35,6 +35,7 @@
 #define SHK_TU_ID 2
 #include "internal.h"
 #include "bounds.cuh"
+#include "prefix.cuh"
 
 namespace shk {
 
@@ -99,7 +100,7 @@ template <int HALF, int BLOCK>
 __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, uint32_t rlo, uint32_t rhi,
                                            uint32_t R, bool wrap, uint32_t Wr, const FastDiv& dw, uint32_t L,
                                            int32_t r_base, uint32_t hs, const DrawParams& P,
-                                           uint32_t (*q)[kQueueCap]) {
+                                           const PhiloxPrefix (&pre)[8], uint32_t (*q)[kQueueCap]) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lo = rlo * Wr, hi = rhi * Wr;
     const uint32_t below = (1u << lane) - 1u;
@@ -112,7 +113,7 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
         if (has) {
             w = q[0][e]; und = q[1][e]; up = q[2][e]; S = q[3][e]; N1 = q[4][e]; N2 = q[5][e]; i = q[6][e];
         }
-        const uint32_t res = draw_rest(block_class(S, N1, N2), w, und, up, hs, P);
+        const uint32_t res = draw_rest_pre(block_class(S, N1, N2), w, und, up, pre, P);
         if (has) dst[i] = res;
     };
     for (uint32_t base = lo + warp * 32; base < hi; base += BLOCK) {
@@ -135,7 +136,7 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
         }
         const BlockClass k = block_class(S, N1, N2);
         uint32_t und, up;
-        draw_first_two(k, w, in ? 0xffffffffu : 0u, hs, P, und, up);
+        draw_first_two_pre(k, w, in ? 0xffffffffu : 0u, pre, P, und, up);
         const bool parked = und != 0u;
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {
@@ -163,6 +164,7 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchArgs a) {
     extern __shared__ uint32_t tile_mem[];
     __shared__ DrawParams P;
+    __shared__ PhiloxPrefix pre[2][8];     // half-steps A and B of the current step
     __shared__ uint32_t qbuf[BLOCK / 32][kBatchQueueFields][kQueueCap];
     __shared__ long long red[kNumObs][BLOCK / 32];
     __shared__ uint32_t item_sh;
@@ -222,9 +224,13 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         long long* partial = reinterpret_cast<long long*>(a.arena + B->scratch_off);
         for (uint32_t j = 0; j < k; ++j) {
             const uint32_t hs = (uint32_t)(2 * (t0 + j));
-            tile_sweep<0, BLOCK>(sg, tu, sweep_lo, R, R, wrap, Wr, dw, L, r_base, hs, P, q);
+            fill_prefixes(pre[0], P, hs);
+            if (tid >= 8 && tid < 16) pre[1][tid - 8] = philox_prefix_dev(P, hs + 1, (int)(tid - 8));
             __syncthreads();
-            tile_sweep<1, BLOCK>(tu, sg, sweep_lo, wrap ? R : R - 1, R, wrap, Wr, dw, L, r_base, hs + 1, P, q);
+            tile_sweep<0, BLOCK>(sg, tu, sweep_lo, R, R, wrap, Wr, dw, L, r_base, hs, P, pre[0], q);
+            __syncthreads();
+            tile_sweep<1, BLOCK>(tu, sg, sweep_lo, wrap ? R : R - 1, R, wrap, Wr, dw, L, r_base, hs + 1, P,
+                                 pre[1], q);
             __syncthreads();
             // sums over the tile's own rows
             int v[kNumObs] = {0, 0, 0, 0, 0};
