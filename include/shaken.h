@@ -115,8 +115,8 @@ int shk_debug_bounds(uint32_t* first_site);
 
 /* ------------------------------------------------------------ thresholds */
 
-/* The six integer thresholds of the per-site draw (Algorithm 3: "+1 iff
- * rand() < e^h / (2 cosh h)"), indexed k = 3*[s = +1] + n, where s is the
+/* The six integer thresholds of the per-site draw (Algorithm 3: the site
+ * becomes +1 when its uniform is below e^h / (2 cosh h)), indexed k = 3*[s = +1] + n, where s is the
  * spin of the site itself and n in {0, 1, 2} the number of +1 neighbours in
  * the field, so that h = q*s + J*(2n - 2).  For h > 0,
  * T = min(2^32 - 1, floor(2^32 / (1 + e^{-2h}))) in IEEE double; for h < 0,
@@ -260,12 +260,38 @@ int shk_philox_peak(int blocks, uint32_t iters, uint32_t* dev_out, void* stream)
 int shk_set_one_launch(int enabled);
 int shk_barrier_timeout_test(unsigned int spin_limit, uint32_t* dev_words, int* timed_out, void* stream);
 
+/* Run-time specialisation of the half-step sweeps (no counterpart in the
+ * paper).  The draw of Eqs. leftTrans / rightTrans compares the random bit
+ * planes with the bits of the three class thresholds of (q, J); compiled with
+ * those thresholds as constants, the masks fold into the logic and the sweep
+ * runs faster.  A bit-packed or int8 half-step whose sweep variant has a
+ * specialised form asks for it at each launch; the first request for a
+ * (variant, thresholds, device) queues a compile with NVRTC for sm_103a
+ * (about a second of host time), kept for the life of the process.  Until
+ * that kernel is ready, and wherever NVRTC cannot be loaded or the compile
+ * fails, the generic kernel runs: the spins and sums are identical either way.
+ * shk_set_specialize(mode), process-wide: 0 off; 1 (default) compile on a
+ * background thread, launches never wait for it (at most 2 tables queued,
+ * 512 per process; requests beyond these run generic); 2 compile at first use
+ * and wait for it.  SHK_EINVAL for another mode; shk_get_specialize returns
+ * the current one.  A compiled kernel is loaded at its first launch on a
+ * stream that is not being captured into a CUDA graph (launches under capture
+ * run generic until then).  shk_specialize_status
+ * reports the entries compiled, failed and still queued and the host seconds
+ * spent compiling (all entries), and copies the last
+ * failure's log (truncated, NUL-terminated) into log when log_bytes > 0; any
+ * pointer may be NULL.  The bounds-checked build never specialises. */
+int shk_set_specialize(int mode);
+int shk_get_specialize(void);
+int shk_specialize_status(int* compiled, int* failed, int* queued, double* compile_seconds, char* log,
+                          size_t log_bytes);
+
 /* ------------------------------------------------------------ lattice handle */
 
 typedef struct shk_lattice shk_lattice;
 
-/* Device bytes a lattice of side L needs: both planes plus a 256-byte
- * observable ring.  0 if (L, layout) is invalid. */
+/* Device bytes a lattice of side L needs: both planes plus 512 bytes of
+ * observable ring and barrier words.  0 if (L, layout) is invalid. */
 size_t shk_lattice_bytes(int L, int layout);
 
 /* Creates a handle over caller-owned device memory dev_mem (at least

@@ -8,8 +8,10 @@ fallback.
 from ._lib import (BITPACK, INIT_ALL_DOWN, INIT_ALL_UP, INIT_RANDOM, INT8, NOBS, ShakenError,
                    lib)
 from .lattice import (Lattice, alloc_plane, halfstep, init_plane, lattice_bytes, pack_bits,
-                      plane_bytes, thresholds, unpack_bits)
+                      plane_bytes, specialize, specialize_status, thresholds, unpack_bits,
+                      wait_specialized)
 
 __all__ = ["BITPACK", "INT8", "INIT_ALL_UP", "INIT_ALL_DOWN", "INIT_RANDOM", "NOBS", "ShakenError",
            "Lattice", "alloc_plane", "halfstep", "init_plane", "lattice_bytes", "pack_bits",
-           "plane_bytes", "thresholds", "unpack_bits", "lib"]
+           "plane_bytes", "specialize", "specialize_status", "thresholds", "unpack_bits",
+           "wait_specialized", "lib"]

@@ -50,6 +50,9 @@ SIGNATURES = {
     "shk_philox_peak": (_i, [_i, _u32, _vp, _vp]),
     "shk_debug_bounds": (_i, [_vp]),
     "shk_set_one_launch": (_i, [_i]),
+    "shk_set_specialize": (_i, [_i]),
+    "shk_get_specialize": (_i, []),
+    "shk_specialize_status": (_i, [_vp, _vp, _vp, _vp, _vp, _sz]),
     "shk_barrier_timeout_test": (_i, [_u32, _vp, _vp, _vp]),
     "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),
     "shk_checkerboard_thresholds": (_i, [_d, _vp]),

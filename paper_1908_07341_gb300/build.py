@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libshaken.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "peak.cu", "sampling.cu", "coop.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "peak.cu", "sampling.cu", "coop.cu", "jit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -45,6 +45,34 @@ LIB_DEBUG = os.path.join(PKG, "libshaken_debug.so")
 BUILD_DEBUG = os.path.join(PKG, "_build_debug")
 
 
+# The device headers that jit.cu compiles at run time, embedded as strings.
+JIT_SOURCES = ["device.cuh", "bounds.cuh", "sweep.cuh", "sweep_kernels.cuh"]
+
+
+def _write_jit_sources(build_dir: str) -> None:
+    delim = "SHKSRC"
+    names, texts = [], []
+    for f in JIT_SOURCES:
+        with open(os.path.join(CSRC, f)) as fh:
+            text = fh.read()
+        if ")" + delim + '"' in text:
+            raise RuntimeError(f"{f} contains the raw-string delimiter")
+        names.append(f'"{f}"')
+        texts.append('R"' + delim + "(" + text + ")" + delim + '"')
+    out = ("// generated by build.py from " + ", ".join(JIT_SOURCES) + "\n"
+           f"static const int kJitSourceCount = {len(JIT_SOURCES)};\n"
+           "static const char* const kJitSourceNames[] = {" + ", ".join(names) + "};\n"
+           "static const char* const kJitSourceTexts[] = {\n" + ",\n".join(texts) + "\n};\n")
+    path = os.path.join(build_dir, "jit_sources.inc")
+    old = None
+    if os.path.exists(path):
+        with open(path) as fh:
+            old = fh.read()
+    if old != out:
+        with open(path, "w") as fh:
+            fh.write(out)
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=(), debug_bounds: bool = False) -> str:
     """Compile if any source is newer than the library; return the library path.
     debug_bounds builds libshaken_debug.so instead, with every kernel's
@@ -57,6 +85,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), debug_boun
     if not force and not _stale(lib_path, deps):
         return lib_path
     os.makedirs(build_dir, exist_ok=True)
+    _write_jit_sources(build_dir)
+    extra_flags = (*extra_flags, "-I", build_dir)
     cc = nvcc()
 
     def compile_one(src: str) -> str:
@@ -74,7 +104,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), debug_boun
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = lib_path + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -9,8 +9,10 @@
 // build checked() is plain pointer arithmetic.
 #pragma once
 
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 #ifndef SHK_TU_ID
 #define SHK_TU_ID 0
@@ -31,6 +33,7 @@ __device__ __forceinline__ T* checked(T* base, uint64_t i, uint64_t n, unsigned 
     return base + i;
 }
 
+#ifndef __CUDACC_RTC__
 // First recorded site of this translation unit (0 = none), cleared.
 static inline unsigned take_bounds_site() {
     unsigned v = 0, z = 0;
@@ -38,13 +41,16 @@ static inline unsigned take_bounds_site() {
     cudaMemcpyToSymbol(g_bounds_site, &z, sizeof z);
     return v;
 }
+#endif
 constexpr bool kBoundsChecked = true;
 #else
 template <class T>
 __device__ __forceinline__ T* checked(T* base, uint64_t i, uint64_t, unsigned) {
     return base + i;
 }
+#ifndef __CUDACC_RTC__
 static inline unsigned take_bounds_site() { return 0; }
+#endif
 constexpr bool kBoundsChecked = false;
 #endif
 

@@ -19,10 +19,24 @@
 // block, with results identical bit for bit to the full comparison.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// runtime compilation (jit.cu): the integer types without the host headers
+typedef unsigned char uint8_t;
+typedef signed char int8_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+#else
 #include <cstdint>
 #include <cuda_runtime.h>
+#endif
 
 namespace shk {
+
+// Plane layouts.
+constexpr int kBitpack = 1;
+constexpr int kInt8 = 2;
 
 // Philox4x32 round multipliers and Weyl key increments (Salmon et al., 2011).
 constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
@@ -203,6 +217,24 @@ __device__ __forceinline__ uint4 philox_call_pre(uint32_t w, const PhiloxPrefix&
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Threshold bit masks of random plane b: all ones where bit 31-b of the
+// class-0 threshold is set (m0), and the changes from class 0 to 1 (d01) and
+// 1 to 2 (d12).  Read from the draw parameters; a kernel compiled at run time
+// for one threshold table (jit.cu) gets the three thresholds as constants
+// instead, so that each plane's mask folds into the logic.
+#ifdef SHK_JIT_U0
+__device__ __forceinline__ uint32_t jit_plane_bit(uint32_t u, int b) {
+    return ((u >> (31 - b)) & 1u) ? 0xffffffffu : 0u;
+}
+#define SHK_PLANE_M0(P, b) jit_plane_bit(SHK_JIT_U0, (b))
+#define SHK_PLANE_D01(P, b) (jit_plane_bit(SHK_JIT_U0, (b)) ^ jit_plane_bit(SHK_JIT_U1, (b)))
+#define SHK_PLANE_D12(P, b) (jit_plane_bit(SHK_JIT_U1, (b)) ^ jit_plane_bit(SHK_JIT_U2, (b)))
+#else
+#define SHK_PLANE_M0(P, b) ((P).m0[b])
+#define SHK_PLANE_D01(P, b) ((P).d01[b])
+#define SHK_PLANE_D12(P, b) ((P).d12[b])
+#endif
+
 // Applies the four planes of call c to the state (und, up) of one block.
 template <class PP>
 __device__ __forceinline__ void apply_planes(const uint4& R, int c, const BlockClass& k, uint32_t& und,
@@ -211,7 +243,7 @@ __device__ __forceinline__ void apply_planes(const uint4& R, int c, const BlockC
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int b = 4 * c + m;
-        const uint32_t g = k.F ^ P.m0[b] ^ (k.Cg & P.d01[b]) ^ (k.C2 & P.d12[b]);
+        const uint32_t g = k.F ^ SHK_PLANE_M0(P, b) ^ (k.Cg & SHK_PLANE_D01(P, b)) ^ (k.C2 & SHK_PLANE_D12(P, b));
         up |= und & ~x[m] & g;
         und &= ~(x[m] ^ g);
     }

@@ -2,6 +2,7 @@
 // kernel launchers (kernels.cu).  Not installed; not part of the ABI.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -10,9 +11,6 @@
 #include "device.cuh"
 
 namespace shk {
-
-constexpr int kBitpack = 1;
-constexpr int kInt8 = 2;
 
 // Geometry of one L x L plane in a layout.
 struct Geometry {
@@ -99,6 +97,17 @@ cudaError_t launch_run_coop(const Geometry& g, void* sigma, void* tau, const Dra
                             uint64_t n, long long* obs, long long* ring, unsigned int* bar,
                             unsigned int spin_limit, cudaStream_t st);
 cudaError_t launch_barrier_probe(unsigned int* bar, unsigned int spin_limit, cudaStream_t st);
+
+// Half-step sweeps compiled at run time for one threshold table (jit.cu).
+// jit_launch launches half `half` of the kernel pair named e0 / e1 and
+// returns true, or returns false without launching when no such kernel is
+// ready (disabled, compile still queued or running, no NVRTC,
+// compile failure).  g_jit_mode: 0 off, 1 compile in the background
+// (default), 2 compile at first use and wait for it.
+struct SweepArgs;
+bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t work_items, const SweepArgs& a,
+                cudaStream_t st, cudaError_t* err);
+extern std::atomic<int> g_jit_mode;
 
 // First bounds-check failure site recorded by each translation unit in the
 // debug build (0 = none; always 0 in the normal build), cleared on read.

@@ -3,10 +3,14 @@
 // a 32-site block, and the launch-grid helper.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+#include "device.cuh"
+#else
 #include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
+#endif
 #include "bounds.cuh"
 
 namespace shk {
@@ -128,6 +132,7 @@ __device__ __forceinline__ void bytes_aligned(const int8_t* __restrict__ pl, uin
     }
 }
 
+#ifndef __CUDACC_RTC__
 // ------------------------------------------------------------ host helpers
 
 int sm_count();
@@ -144,5 +149,7 @@ inline int grid_for(K kernel, int block, uint64_t work_items) {
     const uint64_t need = (work_items + block - 1) / block;
     return (int)std::max<uint64_t>(1, std::min(full, need));
 }
+
+#endif  // __CUDACC_RTC__
 
 }  // namespace shk

@@ -151,6 +151,41 @@ def checkerboard_run(plane: torch.Tensor, L: int, J: float, seed: int, lattice_i
     return out
 
 
+SPECIALIZE_OFF, SPECIALIZE_BACKGROUND, SPECIALIZE_BLOCKING = 0, 1, 2
+
+
+def specialize(mode: int | None = None) -> int:
+    """Run-time specialisation of the sweeps (thresholds compiled in as
+    constants): sets the process-wide mode when given (0 off, 1 compile in the
+    background, the default; 2 compile at first use and wait) and returns the
+    mode now in force."""
+    if mode is not None:
+        check(lib().shk_set_specialize(int(mode)))
+    return int(lib().shk_get_specialize())
+
+
+def specialize_status() -> dict:
+    """Entries compiled, failed and still queued, host seconds spent
+    compiling, and the last failure's log."""
+    c, f, qd, secs = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    log = ctypes.create_string_buffer(8192)
+    check(lib().shk_specialize_status(ctypes.byref(c), ctypes.byref(f), ctypes.byref(qd), ctypes.byref(secs),
+                                      log, len(log)))
+    return {"compiled": c.value, "failed": f.value, "queued": qd.value, "compile_s": secs.value,
+            "log": log.value.decode(errors="replace")}
+
+
+def wait_specialized(timeout_s: float = 60.0) -> dict:
+    """Waits (polling, bounded) until no specialised compile is queued."""
+    import time
+    t0 = time.perf_counter()
+    st = specialize_status()
+    while st["queued"] > 0 and time.perf_counter() - t0 < timeout_s:
+        time.sleep(0.02)
+        st = specialize_status()
+    return st
+
+
 def unpack_bits(words: np.ndarray, L: int) -> np.ndarray:
     """Host view of a bit-packed plane as int8 +/-1 of shape (L, L)."""
     w = np.ascontiguousarray(words).view(np.uint32)[: L * L // 32]

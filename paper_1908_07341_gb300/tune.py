@@ -45,7 +45,9 @@ def size_class(L: int) -> str:
 def time_variants(layout, L: int, launches: int = 20, reps: int = 5) -> dict[int, float]:
     """Mean milliseconds per half-step launch of every variant at side L,
     measured on back-to-back launches replayed from a captured CUDA graph (so
-    host-side launch overhead is excluded)."""
+    host-side launch overhead is excluded).  Unless specialisation is off, each
+    variant is timed in its specialised form (compiled, blocking, before the
+    warm-up launches)."""
     code = layout_code(layout)
     n = _lib.lib().shk_sweep_variant_count(code)
     a, b = alloc_plane(L, layout), alloc_plane(L, layout)
@@ -53,6 +55,9 @@ def time_variants(layout, L: int, launches: int = 20, reps: int = 5) -> dict[int
     T = thresholds(1.0, 0.35)
     acc = torch.zeros(_lib.NOBS, dtype=torch.int64, device=a.device)
     before = get_variant(layout)
+    mode_before = int(_lib.lib().shk_get_specialize())
+    if mode_before != 0:
+        _lib.check(_lib.lib().shk_set_specialize(2))
     out = {}
 
     def enqueue(stream):
@@ -81,6 +86,7 @@ def time_variants(layout, L: int, launches: int = 20, reps: int = 5) -> dict[int
             del g
     finally:
         set_variant(layout, before)
+        _lib.lib().shk_set_specialize(mode_before)
     return out
 
 

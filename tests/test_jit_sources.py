@@ -1,0 +1,116 @@
+"""CPU checks of the run-time specialised sweeps: the embedded device headers
+compile under NVRTC for sm_103a with the three class thresholds as constants,
+for every sweep variant that names a specialised form, and the host-side
+controls behave (no GPU needed: compiling emits a cubin, nothing is launched).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1908_07341_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1908_07341_gb300", "csrc")
+
+
+def _nvrtc():
+    for name in ("libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("NVRTC not loadable")
+
+
+def _name_expressions():
+    """The specialised kernel names of the sweep variant tables."""
+    with open(os.path.join(CSRC, "kernels.cu")) as f:
+        text = f.read()
+    out = []
+    for kernel, args in re.findall(r'SHK_JIT_NAMES\((\w+),\s*"([^"]+)"\)', text):
+        if kernel == "kernel":
+            continue   # the macro's own definition
+        out += [f"shk::{kernel}<0, {args}>", f"shk::{kernel}<1, {args}>"]
+    return out
+
+
+def _compile(nv, names, U):
+    from paper_1908_07341_gb300 import build
+    headers = build.JIT_SOURCES
+    texts = []
+    for h in headers:
+        with open(os.path.join(CSRC, h), "rb") as f:
+            texts.append(f.read())
+    prog = ctypes.c_void_p()
+    hn = (ctypes.c_char_p * len(headers))(*[h.encode() for h in headers])
+    ht = (ctypes.c_char_p * len(headers))(*texts)
+    assert nv.nvrtcCreateProgram(ctypes.byref(prog), b'#include "sweep_kernels.cuh"\n', b"shk_jit.cu",
+                                 len(headers), ht, hn) == 0
+    for n in names:
+        assert nv.nvrtcAddNameExpression(prog, n.encode()) == 0
+    opts = [b"--gpu-architecture=sm_103a", b"-std=c++17"] + [f"-DSHK_JIT_U{i}={u}u".encode()
+                                                             for i, u in enumerate(U)]
+    rc = nv.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    sz = ctypes.c_size_t()
+    nv.nvrtcGetProgramLogSize(prog, ctypes.byref(sz))
+    log = ctypes.create_string_buffer(sz.value + 1)
+    nv.nvrtcGetProgramLog(prog, log)
+    lowered = []
+    cubin = 0
+    if rc == 0:
+        for n in names:
+            p = ctypes.c_char_p()
+            assert nv.nvrtcGetLoweredName(prog, n.encode(), ctypes.byref(p)) == 0
+            lowered.append(p.value.decode())
+        c = ctypes.c_size_t()
+        assert nv.nvrtcGetCUBINSize(prog, ctypes.byref(c)) == 0
+        cubin = c.value
+    nv.nvrtcDestroyProgram(ctypes.byref(prog))
+    return rc, log.value.decode(errors="replace"), lowered, cubin
+
+
+def test_variant_tables_name_specialised_forms():
+    names = _name_expressions()
+    # bit-packed: queue x3, strip-async, strip, queue-128, queue x4; int8: strip-async, strip, queue x2
+    assert len(names) == 2 * 9
+    assert "shk::k_sweep_q<0, 1, 256, 3>" in names
+    assert "shk::k_sweep_strip_async<1, 2, 256, 3, 2>" in names
+
+
+def test_embedded_sources_compile_under_nvrtc():
+    nv = _nvrtc()
+    # thresholds of q = J = 0.5 from the library's own table: the s = +1 half (T[3], T[4], T[5])
+    T = (ctypes.c_uint32 * 6)()
+    assert _lib.lib().shk_thresholds(0.5, 0.5, T) == _lib.OK
+    U = [T[3], T[4], T[5]]
+    names = _name_expressions()
+    rc, log, lowered, cubin = _compile(nv, names, U)
+    assert rc == 0, log
+    assert cubin > 0
+    assert len(set(lowered)) == len(names)
+    assert all(n.startswith("_ZN3shk") for n in lowered)
+
+
+def test_extreme_thresholds_compile():
+    # all-zero and all-one thresholds (q, J at the edges of the table) fold to
+    # constant masks too
+    nv = _nvrtc()
+    names = _name_expressions()[:2]
+    for U in ([0, 0, 0], [0xFFFFFFFF] * 3, [0, 0x80000000, 0xFFFFFFFF]):
+        rc, log, _, cubin = _compile(nv, names, U)
+        assert rc == 0 and cubin > 0, log
+
+
+def test_specialize_controls_host_only():
+    so = _lib.lib()
+    c, f, qd = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int(-1)
+    buf = ctypes.create_string_buffer(64)
+    assert so.shk_specialize_status(ctypes.byref(c), ctypes.byref(f), ctypes.byref(qd), None, buf, 64) == _lib.OK
+    assert c.value >= 0 and f.value >= 0 and qd.value >= 0
+    assert so.shk_specialize_status(None, None, None, None, None, 0) == _lib.OK
+    for mode in (0, 2, 1):
+        assert so.shk_set_specialize(mode) == _lib.OK
+    assert so.shk_set_specialize(3) == _lib.EINVAL
+    assert so.shk_set_specialize(-1) == _lib.EINVAL
