@@ -135,7 +135,8 @@ size_t shk_plane_bytes(int L, int layout);
  * half = SHK_HALF_A, Eq. rightTrans for half = SHK_HALF_B; the sites are
  * independent given src, Eq. "fact").
  *   src, dst   device pointers to distinct planes of shk_plane_bytes(L, layout)
- *              bytes: for A src = sigma, dst = tau; for B src = tau, dst = sigma.
+ *              bytes, 16-byte aligned (SHK_EINVAL otherwise): for A src = sigma,
+ *              dst = tau; for B src = tau, dst = sigma.
  *   T          host array of six thresholds satisfying T[k] + T[5-k] = 2^32
  *              (as produced by shk_thresholds; SHK_EINVAL otherwise).
  *   seed, lattice_id, hs   key and counter words of the random numbers
@@ -168,7 +169,8 @@ int shk_set_sweep_variant(int layout, int variant);
 
 /* Fills a device plane with an initial state: all +1, all -1 or random
  * (+1 iff the site uniform of counter (plane_index, u >> 5, lattice_id,
- * 256 + c) under key init_seed is below 2^31).  Asynchronous. */
+ * 256 + c) under key init_seed is below 2^31).  plane: 16-byte aligned
+ * (SHK_EINVAL otherwise).  Asynchronous. */
 int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
                    uint32_t lattice_id, uint32_t plane_index, void* stream);
 
@@ -176,7 +178,7 @@ int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
  *   out[k]          += sum_x s_x s_{x + (l_k, l_k)}     (SW-NE: (0,0) with (l,l))
  *   out[n_lags + k] += sum_x s_x s_{x + (l_k, -l_k)}    (NW-SE: (0,l) with (l,0))
  * over all x = (i, j) of the torus (translation average times L^2).
- * plane: device bit-packed plane (L % 32 == 0); lags: host array of n_lags
+ * plane: device bit-packed plane (L % 32 == 0, 16-byte aligned); lags: host array of n_lags
  * (1..8) lags in [0, L); out: device int64[2 n_lags], ADDED to (caller
  * zeroes it).  Asynchronous. */
 int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags, int64_t* out, void* stream);
@@ -191,10 +193,10 @@ int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags,
  * uniforms: numbered row by row, a = j (L/2) + floor(i/2), site a takes column
  * a & 31 of the block construction of this header with counter
  * (hs, a >> 5, lattice_id, 512 + c).  plane: device bit-packed sigma
- * (L % 32 == 0), updated in place; dev_obs (nullable): n_steps rows of
+ * (L % 32 == 0, 16-byte aligned), updated in place; dev_obs (nullable): n_steps rows of
  * (M, C_nn) int64, C_nn = sum_x s_x (s_{x up} + s_{x right}), H_G = -J C_nn.
- * Errors: SHK_EINVAL for a bad L, a NULL plane, a non-finite J or steps past
- * 2^31.  Asynchronous. */
+ * Errors: SHK_EINVAL for a bad L, a NULL or misaligned plane, a non-finite J
+ * or steps past 2^31.  Asynchronous. */
 int shk_checkerboard_thresholds(double J, uint32_t out[5]);
 int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t lattice_id, uint64_t t0,
                          uint64_t n_steps, int64_t* dev_obs, void* stream);

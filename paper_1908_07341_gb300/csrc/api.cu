@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -203,6 +204,10 @@ size_t shk_plane_bytes(int L, int layout) {
     return make_geometry(L, layout, &g) ? g.plane_bytes : 0;
 }
 
+// Plane pointers of the stateless calls: the kernels read and write them in
+// 16-byte vectors.
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 int shk_halfstep(int layout, int half, const void* src, void* dst, int L, const uint32_t T[6],
                  uint64_t seed, uint32_t lattice_id, uint32_t hs, int64_t* obs_accum,
                  void* stream) {
@@ -213,6 +218,8 @@ int shk_halfstep(int layout, int half, const void* src, void* dst, int L, const 
         return fail(nullptr, SHK_EINVAL, "shk_halfstep: half must be SHK_HALF_A or SHK_HALF_B");
     if (src == nullptr || dst == nullptr || T == nullptr || src == dst)
         return fail(nullptr, SHK_EINVAL, "shk_halfstep: src, dst, T must be non-NULL and src != dst");
+    if (!aligned16(src) || !aligned16(dst))
+        return fail(nullptr, SHK_EINVAL, "shk_halfstep: src and dst must be 16-byte aligned");
     DrawParams P;
     if (!make_draw_params(seed, lattice_id, T, 0u, &P))
         return fail(nullptr, SHK_EINVAL, "shk_halfstep: threshold table violates T[k] + T[5-k] = 2^32");
@@ -245,6 +252,7 @@ int shk_diag_correlations(const void* plane, int L, const int* lags, int n_lags,
         return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
     if (plane == nullptr || out == nullptr || lags == nullptr)
         return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: NULL argument");
+    if (!aligned16(plane)) return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: plane must be 16-byte aligned");
     if (n_lags < 1 || n_lags > 8) return fail(nullptr, SHK_EINVAL, "shk_diag_correlations: n_lags must be 1..8");
     for (int k = 0; k < n_lags; ++k)
         if (lags[k] < 0 || lags[k] >= L)
@@ -280,6 +288,7 @@ int shk_checkerboard_run(void* plane, int L, double J, uint64_t seed, uint32_t l
     if (!make_geometry(L, kBitpack, &g))
         return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: L=%d must be a multiple of 32 in 32..%d", L, SHK_MAX_L);
     if (plane == nullptr) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: plane is NULL");
+    if (!aligned16(plane)) return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: plane must be 16-byte aligned");
     if (t0 > SHK_MAX_STEP || n_steps > SHK_MAX_STEP - t0)
         return fail(nullptr, SHK_EINVAL, "shk_checkerboard_run: step index would exceed 2^31");
     DrawParams P;
@@ -408,6 +417,7 @@ int shk_init_plane(int layout, void* plane, int L, int kind, uint64_t init_seed,
     if (!make_geometry(L, layout, &g))
         return fail(nullptr, SHK_EINVAL, "shk_init_plane: invalid L=%d for layout %d", L, layout);
     if (plane == nullptr) return fail(nullptr, SHK_EINVAL, "shk_init_plane: plane is NULL");
+    if (!aligned16(plane)) return fail(nullptr, SHK_EINVAL, "shk_init_plane: plane must be 16-byte aligned");
     if (kind != SHK_INIT_ALL_UP && kind != SHK_INIT_ALL_DOWN && kind != SHK_INIT_RANDOM)
         return fail(nullptr, SHK_EINVAL, "shk_init_plane: unknown kind %d", kind);
     const cudaError_t e = launch_init(g, plane, kind, init_seed, lattice_id, plane_index,

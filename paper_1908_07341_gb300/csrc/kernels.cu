@@ -290,7 +290,7 @@ using SweepKernel = void (*)(SweepArgs);
 struct SweepVariant {
     SweepKernel k[2];   // half A, half B
     int block;
-    bool strip;         // needs rows of a multiple of 32 blocks (L % 1024 == 0)
+    int row_blocks;     // rows must hold a multiple of this many blocks (32: L % 1024 == 0)
     const char* name;
     const char* jit[2]; // the same kernels as name expressions for run-time compilation (jit.cu), or null
 };
@@ -300,34 +300,38 @@ struct SweepVariant {
 // The first entry of each table is the default (the fastest measured at
 // L = 16384 on GB300); the autotuner may pick another per size.
 static const SweepVariant kBpVariants[] = {
-    {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, false, "queue-256x3",
+    {{k_sweep_qv<0, 4, 256, 3>, k_sweep_qv<1, 4, 256, 3>}, 256, 4, "queue-v4-256x3",
+     SHK_JIT_NAMES(k_sweep_qv, "4, 256, 3")},
+    {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, 1, "queue-256x3",
      SHK_JIT_NAMES(k_sweep_q, "1, 256, 3")},
-    {{k_sweep_strip_async<0, kBitpack, 256, 3, 4>, k_sweep_strip_async<1, kBitpack, 256, 3, 4>}, 256, true,
+    {{k_sweep_qv<0, 2, 256, 3>, k_sweep_qv<1, 2, 256, 3>}, 256, 2, "queue-v2-256x3",
+     SHK_JIT_NAMES(k_sweep_qv, "2, 256, 3")},
+    {{k_sweep_strip_async<0, kBitpack, 256, 3, 4>, k_sweep_strip_async<1, kBitpack, 256, 3, 4>}, 256, 32,
      "strip-async4-256x3", SHK_JIT_NAMES(k_sweep_strip_async, "1, 256, 3, 4")},
-    {{k_sweep_strip<0, kBitpack, 256, 3>, k_sweep_strip<1, kBitpack, 256, 3>}, 256, true, "strip-256x3",
+    {{k_sweep_strip<0, kBitpack, 256, 3>, k_sweep_strip<1, kBitpack, 256, 3>}, 256, 32, "strip-256x3",
      SHK_JIT_NAMES(k_sweep_strip, "1, 256, 3")},
-    {{k_sweep_q<0, kBitpack, 128, 6>, k_sweep_q<1, kBitpack, 128, 6>}, 128, false, "queue-128x6",
+    {{k_sweep_q<0, kBitpack, 128, 6>, k_sweep_q<1, kBitpack, 128, 6>}, 128, 1, "queue-128x6",
      SHK_JIT_NAMES(k_sweep_q, "1, 128, 6")},
-    {{k_sweep_q<0, kBitpack, 256, 4>, k_sweep_q<1, kBitpack, 256, 4>}, 256, false, "queue-256x4",
+    {{k_sweep_q<0, kBitpack, 256, 4>, k_sweep_q<1, kBitpack, 256, 4>}, 256, 1, "queue-256x4",
      SHK_JIT_NAMES(k_sweep_q, "1, 256, 4")},
-    {{k_sweep_bp<0, 1, false, 256, 1>, k_sweep_bp<1, 1, false, 256, 1>}, 256, false, "plain-256", {nullptr, nullptr}},
+    {{k_sweep_bp<0, 1, false, 256, 1>, k_sweep_bp<1, 1, false, 256, 1>}, 256, 1, "plain-256", {nullptr, nullptr}},
 };
 
 static const SweepVariant kI8Variants[] = {
-    {{k_sweep_strip_async<0, kInt8, 256, 3, 2>, k_sweep_strip_async<1, kInt8, 256, 3, 2>}, 256, true,
+    {{k_sweep_strip_async<0, kInt8, 256, 3, 2>, k_sweep_strip_async<1, kInt8, 256, 3, 2>}, 256, 32,
      "strip-async2-256x3", SHK_JIT_NAMES(k_sweep_strip_async, "2, 256, 3, 2")},
-    {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, true, "strip-256x3",
+    {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, 32, "strip-256x3",
      SHK_JIT_NAMES(k_sweep_strip, "2, 256, 3")},
-    {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, false, "queue-256x3",
+    {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, 1, "queue-256x3",
      SHK_JIT_NAMES(k_sweep_q, "2, 256, 3")},
-    {{k_sweep_q<0, kInt8, 256, 4>, k_sweep_q<1, kInt8, 256, 4>}, 256, false, "queue-256x4",
+    {{k_sweep_q<0, kInt8, 256, 4>, k_sweep_q<1, kInt8, 256, 4>}, 256, 1, "queue-256x4",
      SHK_JIT_NAMES(k_sweep_q, "2, 256, 4")},
-    {{k_sweep_i8a<0, false, 256, 1>, k_sweep_i8a<1, false, 256, 1>}, 256, false, "plain-256", {nullptr, nullptr}},
+    {{k_sweep_i8a<0, false, 256, 1>, k_sweep_i8a<1, false, 256, 1>}, 256, 1, "plain-256", {nullptr, nullptr}},
 };
 
 constexpr int kNumBpVariants = sizeof(kBpVariants) / sizeof(kBpVariants[0]);
 constexpr int kNumI8Variants = sizeof(kI8Variants) / sizeof(kI8Variants[0]);
-constexpr int kBpRowFallback = 0;   // non-strip variant used when rows are too short
+constexpr int kBpRowFallback = 1;   // variant used when rows are too short for the chosen one (queue-256x3)
 constexpr int kI8RowFallback = 2;
 
 static std::atomic<int> g_bp_variant{0};
@@ -359,8 +363,8 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
     if (g.layout == kBitpack || g.aligned) {
         const SweepVariant* table = g.layout == kBitpack ? kBpVariants : kI8Variants;
         int vi = g.layout == kBitpack ? g_bp_variant.load() : g_i8_variant.load();
-        // strip-walk variants need rows of a multiple of 32 blocks (L % 1024 == 0)
-        if (table[vi].strip && (g.Wr % 32) != 0) vi = g.layout == kBitpack ? kBpRowFallback : kI8RowFallback;
+        // strip-walk and vector variants need rows of a multiple of their block count
+        if ((g.Wr % (uint32_t)table[vi].row_blocks) != 0) vi = g.layout == kBitpack ? kBpRowFallback : kI8RowFallback;
         const SweepVariant& v = table[vi];
         cudaError_t e = cudaSuccess;
         if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e)) return e;

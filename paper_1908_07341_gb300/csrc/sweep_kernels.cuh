@@ -1,7 +1,8 @@
 // sweep_kernels.cuh -- the half-step sweep kernels (Eqs. leftTrans /
 // rightTrans over a whole plane, the fused observable sums) and their device
 // helpers: the per-block ILP sweeps (k_sweep_bp, k_sweep_i8a), the two-phase
-// sweep with the warp queue (k_sweep_q), the strip walks (k_sweep_strip,
+// sweep with the warp queue (k_sweep_q) and its vector-load form
+// (k_sweep_qv), the strip walks (k_sweep_strip,
 // k_sweep_strip_async), the generic-L int8 sweep (k_sweep_i8g) and the C_nn
 // tail pass (k_cnn).  Device code only: kernels.cu instantiates them for the
 // launch-shape tables, and jit.cu compiles the same text at run time for one
@@ -290,6 +291,101 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     if (count > 0) {
         __syncwarp();
         drain_queue<HALF, LAYOUT>(a, P, q, head, count, cnn, acc);
+    }
+    finish_step<HALF>(acc, a);
+}
+
+// V consecutive words of a bit plane, vector index i of n (16- or 8-byte load).
+template <int V>
+__device__ __forceinline__ void load_words(const uint32_t* __restrict__ pl, uint32_t i, uint32_t n,
+                                           uint32_t (&o)[V]) {
+    static_assert(V == 2 || V == 4, "vector of 2 or 4 words");
+    if constexpr (V == 4) {
+        const uint4 t = __ldg(checked(reinterpret_cast<const uint4*>(pl), i, n, SHK_SITE));
+        o[0] = t.x;
+        o[1] = t.y;
+        o[2] = t.z;
+        o[3] = t.w;
+    } else {
+        const uint2 t = __ldg(checked(reinterpret_cast<const uint2*>(pl), i, n, SHK_SITE));
+        o[0] = t.x;
+        o[1] = t.y;
+    }
+}
+
+// Bit-packed half-step with V consecutive blocks per thread: the blocks and
+// their row neighbours come in one vector load each and the wrap-around bit
+// in one scalar load, so the index arithmetic and the loads are shared by V
+// blocks.  Each block then takes the two-phase draw with the warp queue
+// exactly as in k_sweep_q (the blocks of a thread one after the other).
+// Needs rows of a multiple of V blocks (L % (32 V) == 0), which also makes
+// the number of vectors a multiple of 32: every lane is active.
+template <int HALF, int V, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_qv(const SweepArgs a) {
+    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    const DrawParams& P = a.P;
+    const uint32_t* __restrict__ src = static_cast<const uint32_t*>(a.src);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
+    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[3] = {0, 0, 0};
+    uint32_t head = 0;
+    int count = 0;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t nvec = a.nblocks / V, Wv = a.Wr / V;
+    for (uint32_t base = gwarp * 32; base < nvec; base += stride) {
+        const uint32_t v = base + lane;
+        const uint32_t w0 = v * V;
+        const uint32_t row = fdiv(w0, a.div_row);
+        const uint32_t col = w0 - row * a.Wr;
+        uint32_t S[V], N1[V];
+        load_words<V>(src, v, nvec, S);
+        if (HALF == 0) {
+            load_words<V>(src, row > 0 ? v - Wv : v + nvec - Wv, nvec, N1);
+        } else {
+            load_words<V>(src, row + 1 < a.L ? v + Wv : v + Wv - nvec, nvec, N1);
+        }
+        // the word left of the first block (A) or right of the last one (B)
+        const uint32_t x = HALF == 0 ? __ldg(checked(src, col > 0 ? w0 - 1 : w0 + a.Wr - 1, a.nblocks, SHK_SITE))
+                                     : __ldg(checked(src, col + V < a.Wr ? w0 + V : w0 + V - a.Wr, a.nblocks,
+                                                     SHK_SITE));
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const uint32_t w = w0 + k;
+            const uint32_t N2 = HALF == 0 ? (S[k] << 1) | ((k == 0 ? x : S[k - 1]) >> 31)
+                                          : (S[k] >> 1) | ((k == V - 1 ? x : S[k + 1]) << 31);
+            const BlockClass c = block_class(S[k], N1[k], N2);
+            uint32_t und, up;
+            draw_first_two_pre(c, w, 0xffffffffu, a.pre, P, und, up);
+            const bool parked = und != 0u;
+            const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+            if (parked) {
+                const uint32_t i = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+                q[0][i] = w;
+                q[1][i] = und;
+                q[2][i] = up;
+                q[3][i] = S[k];
+                q[4][i] = N1[k];
+                q[5][i] = N2;
+            } else {
+                finish_block<HALF, kBitpack>(a, w, up, S[k], N1[k], N2, cnn, acc);
+            }
+            count += __popc(mask);
+            if (count >= 32) {
+                __syncwarp();
+                drain_queue<HALF, kBitpack>(a, P, q, head, 32, cnn, acc);
+                __syncwarp();
+                head = (head + 32) & (kQueueCap - 1);
+                count -= 32;
+            }
+        }
+    }
+    if (count > 0) {
+        __syncwarp();
+        drain_queue<HALF, kBitpack>(a, P, q, head, count, cnn, acc);
     }
     finish_step<HALF>(acc, a);
 }

@@ -5,7 +5,8 @@ the site, the half-step and the seed), so the choice is purely about speed.
 The tuner times each variant with CUDA events on the caller's stream over a
 few launches of shk_halfstep on scratch planes of the requested size, sets the
 fastest process-wide through the C ABI, and caches the choice per
-(GPU name, layout, size class) in a JSON file.
+(GPU name, layout, size class) in a JSON file (an entry made for another list
+of variants is timed again).
 """
 from __future__ import annotations
 
@@ -116,7 +117,7 @@ def autotune(layout, L: int, use_cache: bool = True, stream=None) -> int:
     key = f"{torch.cuda.get_device_name()}|{layout_code(layout)}|{size_class(L)}"
     with _lock:
         cache = _load_cache() if use_cache else {}
-        if key in cache:
+        if key in cache and cache[key].get("names") == variant_names(layout):
             best = int(cache[key]["variant"])
         else:
             times = time_variants(layout, L)

@@ -73,8 +73,9 @@ def _compile(nv, names, U):
 
 def test_variant_tables_name_specialised_forms():
     names = _name_expressions()
-    # bit-packed: queue x3, strip-async, strip, queue-128, queue x4; int8: strip-async, strip, queue x2
-    assert len(names) == 2 * 9
+    # bit-packed: queue-v4, queue x3, queue-v2, strip-async, strip, queue-128, queue x4;
+    # int8: strip-async, strip, queue x2
+    assert len(names) == 2 * 11
     assert "shk::k_sweep_q<0, 1, 256, 3>" in names
     assert "shk::k_sweep_strip_async<1, 2, 256, 3, 2>" in names
 

@@ -88,6 +88,21 @@ def test_bad_arguments_are_rejected_without_a_gpu(so):
     assert so.shk_strerror(_lib.EBUSY) == b"busy"
 
 
+def test_misaligned_planes_are_rejected_without_a_gpu(so):
+    # the kernels move planes in 16-byte vectors: a misaligned pointer is an
+    # argument error, reported before anything is launched
+    T = np.zeros(6, dtype=np.uint32)
+    assert so.shk_thresholds(0.5, 0.5, T.ctypes.data) == _lib.OK
+    for layout in (_lib.BITPACK, _lib.INT8):
+        assert so.shk_halfstep(layout, 0, 256 + 4, 1 << 20, 64, T.ctypes.data, 1, 0, 0, None, None) == _lib.EINVAL
+        assert b"aligned" in so.shk_last_error(None)
+        assert so.shk_halfstep(layout, 1, 256, (1 << 20) + 8, 64, T.ctypes.data, 1, 0, 0, None, None) == _lib.EINVAL
+        assert so.shk_init_plane(layout, 256 + 1, 64, _lib.INIT_RANDOM, 1, 0, 0, None) == _lib.EINVAL
+    lags = np.array([1], dtype=np.int32)
+    assert so.shk_diag_correlations(256 + 4, 64, lags.ctypes.data, 1, 512, None) == _lib.EINVAL
+    assert so.shk_checkerboard_run(ctypes.c_void_p(256 + 12), 64, 0.4, 1, 0, 0, 1, None, None) == _lib.EINVAL
+
+
 def test_handle_state_checks_without_a_gpu(so):
     # A handle over a fake (never dereferenced) aligned address: configuration
     # calls are host-only, and running before set_params is refused.
