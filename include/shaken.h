@@ -287,6 +287,14 @@ int shk_set_specialize(int mode);
 int shk_get_specialize(void);
 int shk_specialize_status(int* compiled, int* failed, int* queued, double* compile_seconds, char* log,
                           size_t log_bytes);
+/* Queues the compile of the specialised form of sweep variant `variant` of
+ * `layout` for the thresholds of (q, J), without launching anything and
+ * without a GPU (the first launch on a device loads it); with wait != 0 it
+ * also waits for the compile.  SHK_EINVAL for non-finite q or J, an unknown
+ * variant or one without a specialised form; SHK_ESTATE when specialisation
+ * is off, NVRTC cannot be loaded, the compile failed (wait != 0) or in the
+ * bounds-checked build.  For callers that know their tables ahead of time. */
+int shk_specialize_prepare(int layout, int variant, double q, double J, int wait);
 
 /* ------------------------------------------------------------ lattice handle */
 

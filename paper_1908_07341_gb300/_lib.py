@@ -52,6 +52,7 @@ SIGNATURES = {
     "shk_set_one_launch": (_i, [_i]),
     "shk_set_specialize": (_i, [_i]),
     "shk_get_specialize": (_i, []),
+    "shk_specialize_prepare": (_i, [_i, _i, _d, _d, _i]),
     "shk_specialize_status": (_i, [_vp, _vp, _vp, _vp, _vp, _sz]),
     "shk_barrier_timeout_test": (_i, [_u32, _vp, _vp, _vp]),
     "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),

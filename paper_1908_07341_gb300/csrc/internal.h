@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstddef>
+#include <string>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
@@ -108,6 +109,13 @@ struct SweepArgs;
 bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t work_items, const SweepArgs& a,
                 cudaStream_t st, cudaError_t* err);
 extern std::atomic<int> g_jit_mode;
+// Queues (wait: and waits for) the specialised compile of sweep variant
+// `variant` of `layout` for threshold table T; SHK_OK or an error status with
+// the reason in *why.
+int jit_prepare(int layout, int variant, const uint32_t T[6], bool wait, std::string* why);
+// The run-time compilation names of a sweep variant (null when it has none)
+// and its block size; false for an unknown (layout, variant).
+bool sweep_variant_jit(int layout, int variant, const char** e0, const char** e1, int* block);
 
 // First bounds-check failure site recorded by each translation unit in the
 // debug build (0 = none; always 0 in the normal build), cleared on read.

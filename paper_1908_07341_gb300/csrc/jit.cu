@@ -84,23 +84,27 @@ const Nvrtc& nvrtc() {
     return n;
 }
 
-// One (kernel pair, threshold table, device) entry.  The compile (NVRTC,
-// host only) runs on a background thread; the module load and the launches
-// happen on the launching thread.
+// One (kernel pair, threshold table) entry.  The compile (NVRTC, host only)
+// runs on a background thread and leaves a cubin; each device loads it on a
+// launching thread, at its first launch there.
 struct JitEntry {
-    enum State { kQueued, kCompiled, kLoaded, kFailed };
+    enum State { kQueued, kCompiled, kFailed };
     State state = kQueued;
     std::string e[2];
     uint32_t U[3] = {0, 0, 0};
     int block = 0;
     std::vector<char> cubin;
     std::string lowered[2];
-    cudaLibrary_t lib = nullptr;
-    cudaKernel_t k[2] = {nullptr, nullptr};
-    int per_sm[2] = {0, 0};
+    struct Loaded {
+        bool ok = false;
+        cudaLibrary_t lib = nullptr;
+        cudaKernel_t k[2] = {nullptr, nullptr};
+        int per_sm[2] = {0, 0};
+    };
+    std::map<int, Loaded> dev;   // by device ordinal
 };
 
-using Key = std::tuple<int, std::string, uint32_t, uint32_t, uint32_t>;
+using Key = std::tuple<std::string, uint32_t, uint32_t, uint32_t>;
 
 std::mutex g_mu;                          // guards everything below
 std::condition_variable g_cv;             // signalled when an entry leaves kQueued, or on stop
@@ -111,7 +115,7 @@ bool g_stop = false;
 std::string g_last_log;
 double g_compile_s = 0.0;                 // host seconds spent compiling, all entries
 
-constexpr size_t kMaxQueued = 2;          // tables waiting beyond this are not queued (generic kernel)
+constexpr size_t kMaxQueued = 2;          // launches queue no table beyond this (generic kernel meanwhile)
 constexpr size_t kMaxEntries = 512;       // bound on compiled tables per process
 
 // NVRTC compile of the entry's two kernels with its thresholds as
@@ -161,6 +165,30 @@ bool compile_cubin(JitEntry* en, std::string* log_out) {
     return ok;
 }
 
+// A small compile on the calling thread before the worker starts.  NVRTC
+// builds internal state on first use, and registers its teardown at exit
+// then; doing that here, before stop_worker is registered, makes the
+// teardown run after stop_worker has waited for any compile in flight
+// (otherwise a process that exits during a background compile can crash
+// or hang in its exit handlers).
+void warm_up() {
+    const Nvrtc& n = nvrtc();
+    nvrtcProgram prog = nullptr;
+    const char* src =
+        "namespace shk_warm { template <int K> __global__ void k(unsigned* p) { p[threadIdx.x] = __umulhi(p[0], K); } }\n";
+    if (n.create(&prog, src, "shk_warm.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return;
+    const char* name = "shk_warm::k<3>";
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17"};
+    const char* low = nullptr;
+    size_t sz = 0;
+    if (n.add_name(prog, name) == NVRTC_SUCCESS && n.compile(prog, 2, opts) == NVRTC_SUCCESS &&
+        n.lowered(prog, name, &low) == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS && sz > 0) {
+        std::vector<char> cubin(sz);
+        n.cubin(prog, cubin.data());
+    }
+    n.destroy(&prog);
+}
+
 void worker_main() {
     std::unique_lock<std::mutex> lock(g_mu);
     for (;;) {
@@ -181,8 +209,8 @@ void worker_main() {
     }
 }
 
-// Runs at process exit, before the libraries' own teardown: lets a compile
-// in flight finish and stops the worker.
+// Runs at process exit, before NVRTC's own teardown: lets a compile in
+// flight finish and stops the worker.
 void stop_worker() {
     std::thread* t = nullptr;
     {
@@ -194,28 +222,57 @@ void stop_worker() {
     if (t && t->joinable()) t->join();
 }
 
-// Loads a compiled entry on the calling thread (kCompiled -> kLoaded or kFailed).
-void load(JitEntry* en) {
-    if (cudaLibraryLoadData(&en->lib, en->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
+// The entry of (e0, U), queued for compile when new.  force: queue even past
+// kMaxQueued.  Null when no entry can be made (stopping, too many entries,
+// queue full, no NVRTC).  Called with g_mu held.
+JitEntry* find_or_queue(const char* e0, const char* e1, int block, const uint32_t U[3], bool force) {
+    const Key key = std::make_tuple(std::string(e0), U[0], U[1], U[2]);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) return it->second;
+    if (g_stop || g_cache.size() >= kMaxEntries || (!force && g_queue.size() >= kMaxQueued)) return nullptr;
+    if (!nvrtc().ok) {
+        g_last_log = "NVRTC could not be loaded";
+        return nullptr;
+    }
+    JitEntry* en = new JitEntry;
+    en->e[0] = e0;
+    en->e[1] = e1;
+    std::copy(U, U + 3, en->U);
+    en->block = block;
+    g_cache.emplace(key, en);
+    g_queue.push_back(en);
+    if (g_worker == nullptr) {
+        warm_up();
+        std::atexit(stop_worker);
+        g_worker = new std::thread(worker_main);
+    }
+    g_cv.notify_all();
+    return en;
+}
+
+// The kernels of a compiled entry on device dev, loaded now if needed (on
+// the calling thread); null if loading failed.  Called with g_mu held.
+const JitEntry::Loaded* loaded_on(JitEntry* en, int dev) {
+    auto it = en->dev.find(dev);
+    if (it != en->dev.end()) return it->second.ok ? &it->second : nullptr;
+    JitEntry::Loaded& l = en->dev[dev];
+    if (cudaLibraryLoadData(&l.lib, en->cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess) {
         cudaGetLastError();
-        en->state = JitEntry::kFailed;
         g_last_log = "cudaLibraryLoadData failed";
-        return;
+        return nullptr;
     }
     for (int h = 0; h < 2; ++h) {
-        if (cudaLibraryGetKernel(&en->k[h], en->lib, en->lowered[h].c_str()) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&en->per_sm[h], reinterpret_cast<const void*>(en->k[h]),
+        if (cudaLibraryGetKernel(&l.k[h], l.lib, en->lowered[h].c_str()) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l.per_sm[h], reinterpret_cast<const void*>(l.k[h]),
                                                           en->block, 0) != cudaSuccess) {
             cudaGetLastError();
-            en->state = JitEntry::kFailed;
             g_last_log = "loading a compiled kernel failed";
-            return;
+            return nullptr;
         }
-        if (en->per_sm[h] <= 0) en->per_sm[h] = 1;
+        if (l.per_sm[h] <= 0) l.per_sm[h] = 1;
     }
-    en->cubin.clear();
-    en->cubin.shrink_to_fit();
-    en->state = JitEntry::kLoaded;
+    l.ok = true;
+    return &l;
 }
 
 }  // namespace
@@ -248,35 +305,18 @@ bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t wo
     uint32_t U[3];
     thresholds_of(a.P, U);
     int dev = 0;
-    cudaGetDevice(&dev);
-    JitEntry* en = nullptr;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const JitEntry::Loaded* l = nullptr;
     {
         std::unique_lock<std::mutex> lock(g_mu);
-        const Key key = std::make_tuple(dev, std::string(e0), U[0], U[1], U[2]);
-        auto it = g_cache.find(key);
-        if (it == g_cache.end()) {
-            if (g_stop || g_cache.size() >= kMaxEntries || (mode == 1 && g_queue.size() >= kMaxQueued)) return false;
-            if (!nvrtc().ok) {
-                g_last_log = "NVRTC could not be loaded";
-                return false;
-            }
-            en = new JitEntry;
-            en->e[0] = e0;
-            en->e[1] = e1;
-            std::copy(U, U + 3, en->U);
-            en->block = block;
-            g_cache.emplace(key, en);
-            g_queue.push_back(en);
-            if (g_worker == nullptr) {
-                g_worker = new std::thread(worker_main);
-                std::atexit(stop_worker);
-            }
-            g_cv.notify_all();
-        } else {
-            en = it->second;
-        }
+        JitEntry* en = find_or_queue(e0, e1, block, U, mode == 2);
+        if (en == nullptr) return false;
         if (mode == 2) g_cv.wait(lock, [en] { return en->state != JitEntry::kQueued || g_stop; });
-        if (en->state == JitEntry::kCompiled) {
+        if (en->state != JitEntry::kCompiled) return false;
+        if (en->dev.find(dev) == en->dev.end()) {
             // loading a module is not allowed while the stream is being
             // captured into a graph: launch generic until a later call loads it
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -285,16 +325,56 @@ bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t wo
                 return false;
             }
             if (cs != cudaStreamCaptureStatusNone) return false;
-            load(en);
         }
-        if (en->state != JitEntry::kLoaded) return false;
+        l = loaded_on(en, dev);
+        if (l == nullptr) return false;
     }
-    const uint64_t full = (uint64_t)en->per_sm[half] * sm_count();
+    const uint64_t full = (uint64_t)l->per_sm[half] * sm_count();
     const uint64_t need = ((uint64_t)work_items + block - 1) / block;
     const int grid = (int)std::max<uint64_t>(1, std::min(full, need));
     void* args[] = {const_cast<SweepArgs*>(&a)};
-    *err = cudaLaunchKernel(reinterpret_cast<const void*>(en->k[half]), dim3(grid), dim3(block), args, 0, st);
+    *err = cudaLaunchKernel(reinterpret_cast<const void*>(l->k[half]), dim3(grid), dim3(block), args, 0, st);
     return true;
+#endif
+}
+
+// Queues (wait: and waits for) the compile of the specialised form of a
+// sweep variant for one threshold table, without launching anything.
+int jit_prepare(int layout, int variant, const uint32_t T[6], bool wait, std::string* why) {
+#ifdef SHK_DEBUG_BOUNDS
+    (void)layout, (void)variant, (void)T, (void)wait;
+    *why = "the bounds-checked build never specialises";
+    return SHK_ESTATE;
+#else
+    const char* e0 = nullptr;
+    const char* e1 = nullptr;
+    int block = 0;
+    if (!sweep_variant_jit(layout, variant, &e0, &e1, &block)) {
+        *why = "no such variant";
+        return SHK_EINVAL;
+    }
+    if (e0 == nullptr) {
+        *why = "this variant has no specialised form";
+        return SHK_EINVAL;
+    }
+    if (g_jit_mode.load() == 0) {
+        *why = "specialisation is off";
+        return SHK_ESTATE;
+    }
+    const uint32_t U[3] = {T[3], T[4], T[5]};
+    std::unique_lock<std::mutex> lock(g_mu);
+    JitEntry* en = find_or_queue(e0, e1, block, U, true);
+    if (en == nullptr) {
+        *why = g_last_log.empty() ? std::string("no more entries can be compiled") : g_last_log;
+        return SHK_ESTATE;
+    }
+    if (!wait) return SHK_OK;
+    g_cv.wait(lock, [en] { return en->state != JitEntry::kQueued || g_stop; });
+    if (en->state != JitEntry::kCompiled) {
+        *why = g_last_log.empty() ? std::string("the compile did not finish") : g_last_log;
+        return SHK_ESTATE;
+    }
+    return SHK_OK;
 #endif
 }
 
@@ -315,9 +395,11 @@ int shk_specialize_status(int* compiled, int* failed, int* queued, double* compi
     std::lock_guard<std::mutex> lock(shk::g_mu);
     int c = 0, f = 0, qd = 0;
     for (const auto& kv : shk::g_cache) {
-        const auto s = kv.second->state;
-        if (s == shk::JitEntry::kFailed) ++f;
-        else if (s == shk::JitEntry::kQueued) ++qd;
+        const shk::JitEntry* en = kv.second;
+        bool load_failed = false;
+        for (const auto& d : en->dev) load_failed |= !d.second.ok;
+        if (en->state == shk::JitEntry::kFailed || load_failed) ++f;
+        else if (en->state == shk::JitEntry::kQueued) ++qd;
         else ++c;
     }
     if (compiled) *compiled = c;
@@ -330,6 +412,18 @@ int shk_specialize_status(int* compiled, int* failed, int* queued, double* compi
         log[n] = '\0';
     }
     return SHK_OK;
+}
+
+int shk_specialize_prepare(int layout, int variant, double q, double J, int wait) {
+    uint32_t T[6];
+    if (shk::host_thresholds(q, J, T) != SHK_OK) {
+        shk::set_thread_error("shk_specialize_prepare: q and J must be finite");
+        return SHK_EINVAL;
+    }
+    std::string why;
+    const int rc = shk::jit_prepare(layout, variant, T, wait != 0, &why);
+    if (rc != SHK_OK) shk::set_thread_error(("shk_specialize_prepare: " + why).c_str());
+    return rc;
 }
 
 }  // extern "C"

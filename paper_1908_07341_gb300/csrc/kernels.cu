@@ -341,6 +341,15 @@ int sweep_variant_count(int layout) {
     return layout == kBitpack ? kNumBpVariants : layout == kInt8 ? kNumI8Variants : 0;
 }
 
+bool sweep_variant_jit(int layout, int v, const char** e0, const char** e1, int* block) {
+    if (v < 0 || v >= sweep_variant_count(layout)) return false;
+    const SweepVariant& sv = layout == kBitpack ? kBpVariants[v] : kI8Variants[v];
+    *e0 = sv.jit[0];
+    *e1 = sv.jit[1];
+    *block = sv.block;
+    return true;
+}
+
 const char* sweep_variant_name(int layout, int v) {
     if (v < 0 || v >= sweep_variant_count(layout)) return nullptr;
     return layout == kBitpack ? kBpVariants[v].name : kI8Variants[v].name;

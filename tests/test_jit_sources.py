@@ -6,6 +6,8 @@ controls behave (no GPU needed: compiling emits a cubin, nothing is launched).
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -115,3 +117,53 @@ def test_specialize_controls_host_only():
         assert so.shk_set_specialize(mode) == _lib.OK
     assert so.shk_set_specialize(3) == _lib.EINVAL
     assert so.shk_set_specialize(-1) == _lib.EINVAL
+
+
+def test_prepare_compiles_without_a_gpu():
+    _nvrtc()
+    so = _lib.lib()
+    assert so.shk_specialize_prepare(_lib.BITPACK, 0, 0.9, 0.41, 1) == _lib.OK
+    c, f, qd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    secs = ctypes.c_double()
+    assert so.shk_specialize_status(ctypes.byref(c), ctypes.byref(f), ctypes.byref(qd), ctypes.byref(secs),
+                                    None, 0) == _lib.OK
+    assert c.value >= 1 and f.value == 0 and secs.value > 0
+    # the same table again is already there
+    assert so.shk_specialize_prepare(_lib.BITPACK, 0, 0.9, 0.41, 1) == _lib.OK
+    c2 = ctypes.c_int()
+    so.shk_specialize_status(ctypes.byref(c2), None, None, None, None, 0)
+    assert c2.value == c.value
+    n_bp = so.shk_sweep_variant_count(_lib.BITPACK)
+    assert so.shk_specialize_prepare(_lib.BITPACK, n_bp - 1, 0.9, 0.41, 1) == _lib.EINVAL   # plain: none
+    assert b"no specialised form" in so.shk_last_error(None)
+    assert so.shk_specialize_prepare(_lib.BITPACK, n_bp, 0.9, 0.41, 1) == _lib.EINVAL
+    assert so.shk_specialize_prepare(_lib.INT8, 0, float("nan"), 0.41, 1) == _lib.EINVAL
+    assert so.shk_set_specialize(0) == _lib.OK
+    try:
+        assert so.shk_specialize_prepare(_lib.BITPACK, 0, 0.9, 0.41, 1) == _lib.ESTATE
+    finally:
+        so.shk_set_specialize(1)
+
+
+_EXIT_CHILD = r"""
+import ctypes, sys, time
+so = ctypes.CDLL(sys.argv[1])
+so.shk_specialize_prepare.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+for k in range(3):
+    assert so.shk_specialize_prepare(1, 0, 0.5 + 0.01 * k, 0.3, 0) == 0
+time.sleep(float(sys.argv[2]))
+print("exiting", flush=True)
+"""
+
+
+@pytest.mark.parametrize("delay", [0.0, 0.15, 0.4, 0.8])
+def test_exit_during_a_background_compile_is_clean(delay):
+    """A process that exits while compiles are queued or running waits for
+    the one in flight and exits normally (no crash or hang in NVRTC's exit
+    handlers)."""
+    _nvrtc()
+    lib_path = _lib.LIB_PATH
+    r = subprocess.run([sys.executable, "-c", _EXIT_CHILD, lib_path, str(delay)], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    assert "exiting" in r.stdout
