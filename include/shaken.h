@@ -273,9 +273,10 @@ int shk_barrier_timeout_test(unsigned int spin_limit, uint32_t* dev_words, int* 
  * that kernel is ready, and wherever NVRTC cannot be loaded or the compile
  * fails, the generic kernel runs: the spins and sums are identical either way.
  * shk_set_specialize(mode), process-wide: 0 off; 1 (default) compile on a
- * background thread, launches never wait for it (at most 2 tables queued,
- * 512 per process; requests beyond these run generic); 2 compile at first use
- * and wait for it.  SHK_EINVAL for another mode; shk_get_specialize returns
+ * background thread, launches do not wait for it (at most 2 tables queued,
+ * 512 per process; requests beyond these run generic), except for the
+ * process's first compile, which runs on the calling thread; 2 compile at
+ * first use and wait for it.  SHK_EINVAL for another mode; shk_get_specialize returns
  * the current one.  A compiled kernel is loaded at its first launch on a
  * stream that is not being captured into a CUDA graph (launches under capture
  * run generic until then).  shk_specialize_status
@@ -295,6 +296,12 @@ int shk_specialize_status(int* compiled, int* failed, int* queued, double* compi
  * is off, NVRTC cannot be loaded, the compile failed (wait != 0) or in the
  * bounds-checked build.  For callers that know their tables ahead of time. */
 int shk_specialize_prepare(int layout, int variant, double q, double J, int wait);
+/* Stops the background compiler: waits for the compile in flight, if any,
+ * and queues no more (tables not yet compiled then run generic).  Idempotent.
+ * A process should call it before it exits while compiles may be running;
+ * the library also does so from an exit handler, and the Python binding from
+ * its interpreter-exit hook, which runs before any C exit handler. */
+int shk_specialize_shutdown(void);
 
 /* ------------------------------------------------------------ lattice handle */
 

@@ -6,6 +6,7 @@ fallback -- importing the binding without the built library raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import functools
 import os
@@ -53,6 +54,7 @@ SIGNATURES = {
     "shk_set_specialize": (_i, [_i]),
     "shk_get_specialize": (_i, []),
     "shk_specialize_prepare": (_i, [_i, _i, _d, _d, _i]),
+    "shk_specialize_shutdown": (_i, []),
     "shk_specialize_status": (_i, [_vp, _vp, _vp, _vp, _vp, _sz]),
     "shk_barrier_timeout_test": (_i, [_u32, _vp, _vp, _vp]),
     "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),
@@ -116,6 +118,9 @@ def lib() -> ctypes.CDLL:
         fn = getattr(so, name)
         fn.restype = res
         fn.argtypes = args
+    # interpreter exit runs this before any C exit handler: a run-time compile
+    # still in flight finishes before the process tears anything down
+    atexit.register(so.shk_specialize_shutdown)
     return so
 
 

@@ -8,8 +8,9 @@
 // parameters.  This file compiles the sweep kernels' own source text (the
 // headers are embedded at build time) with NVRTC for sm_103a, once per
 // (launch shape, threshold table, device), and launches the result through
-// the runtime's library API.  The compile runs on a background thread, so a
-// launch never waits for it (unless the blocking mode asks to): until the
+// the runtime's library API.  After the first compile of the process (which
+// runs on the calling thread), compiles run on a background thread, so a
+// launch does not wait for them (unless the blocking mode asks to): until the
 // specialised kernel is ready, and whenever NVRTC cannot be loaded or the
 // compile fails, the caller launches the generic kernel, which computes the
 // same spins and sums.
@@ -165,30 +166,6 @@ bool compile_cubin(JitEntry* en, std::string* log_out) {
     return ok;
 }
 
-// A small compile on the calling thread before the worker starts.  NVRTC
-// builds internal state on first use, and registers its teardown at exit
-// then; doing that here, before stop_worker is registered, makes the
-// teardown run after stop_worker has waited for any compile in flight
-// (otherwise a process that exits during a background compile can crash
-// or hang in its exit handlers).
-void warm_up() {
-    const Nvrtc& n = nvrtc();
-    nvrtcProgram prog = nullptr;
-    const char* src =
-        "namespace shk_warm { template <int K> __global__ void k(unsigned* p) { p[threadIdx.x] = __umulhi(p[0], K); } }\n";
-    if (n.create(&prog, src, "shk_warm.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) return;
-    const char* name = "shk_warm::k<3>";
-    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17"};
-    const char* low = nullptr;
-    size_t sz = 0;
-    if (n.add_name(prog, name) == NVRTC_SUCCESS && n.compile(prog, 2, opts) == NVRTC_SUCCESS &&
-        n.lowered(prog, name, &low) == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS && sz > 0) {
-        std::vector<char> cubin(sz);
-        n.cubin(prog, cubin.data());
-    }
-    n.destroy(&prog);
-}
-
 void worker_main() {
     std::unique_lock<std::mutex> lock(g_mu);
     for (;;) {
@@ -209,8 +186,9 @@ void worker_main() {
     }
 }
 
-// Runs at process exit, before NVRTC's own teardown: lets a compile in
-// flight finish and stops the worker.
+// Lets a compile in flight finish and stops the worker; idempotent.  Runs at
+// process exit (registered after NVRTC's own teardown, so before it), and
+// from shk_specialize_shutdown.
 void stop_worker() {
     std::thread* t = nullptr;
     {
@@ -240,12 +218,23 @@ JitEntry* find_or_queue(const char* e0, const char* e1, int block, const uint32_
     std::copy(U, U + 3, en->U);
     en->block = block;
     g_cache.emplace(key, en);
-    g_queue.push_back(en);
     if (g_worker == nullptr) {
-        warm_up();
+        // The first compile of the process runs here, on the calling thread.
+        // NVRTC builds internal state on first use and registers its teardown
+        // at exit then; registering stop_worker only afterwards makes it run
+        // before that teardown, so an exit during a later background compile
+        // waits for it instead of tearing NVRTC down under it (which crashed).
+        std::string log;
+        const auto t0 = std::chrono::steady_clock::now();
+        const bool ok = compile_cubin(en, &log);
+        g_compile_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        en->state = ok ? JitEntry::kCompiled : JitEntry::kFailed;
+        if (!ok) g_last_log = log;
         std::atexit(stop_worker);
         g_worker = new std::thread(worker_main);
+        return en;
     }
+    g_queue.push_back(en);
     g_cv.notify_all();
     return en;
 }
@@ -411,6 +400,11 @@ int shk_specialize_status(int* compiled, int* failed, int* queued, double* compi
         std::memcpy(log, shk::g_last_log.data(), n);
         log[n] = '\0';
     }
+    return SHK_OK;
+}
+
+int shk_specialize_shutdown(void) {
+    shk::stop_worker();
     return SHK_OK;
 }
 

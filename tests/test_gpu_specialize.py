@@ -3,6 +3,9 @@ the same spins and sums as the generic kernels and the oracle, for every
 sweep variant, both layouts, and threshold tables at the edges of the
 range; and they are the kernels that actually ran."""
 import ctypes
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -128,3 +131,28 @@ def test_disabled_compiles_nothing():
     _run(1024, "bitpack", 0.9, 0.123, 2, False)
     c1, f1, _ = _status()
     assert (c1, f1) == (c0, f0)
+
+
+_EXIT_CHILD = r"""
+import sys
+import paper_1908_07341_gb300 as shk
+shk.specialize(1)
+lat = shk.Lattice(1024, "bitpack").set_seed(1, 0).set_params(0.8, 0.31).init("random", init_seed=1)
+lat.run(2)                      # the process's first compile, on this thread
+for k in range(3):              # more tables: compiled in the background
+    lat.set_params(0.8, 0.32 + 0.01 * k)
+    lat.run(2)
+lat.read_observables()
+print("exiting", shk.specialize_status()["queued"], flush=True)
+"""
+
+
+def test_exit_with_compiles_in_flight_is_clean():
+    """A process that exits right after queuing background compiles waits for
+    the one in flight and exits normally."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", _EXIT_CHILD], capture_output=True, text=True, timeout=300,
+                           cwd=root)
+        assert r.returncode == 0, (r.returncode, r.stdout[-500:], r.stderr[-2000:])
+        assert "exiting" in r.stdout

@@ -156,14 +156,49 @@ print("exiting", flush=True)
 """
 
 
+_EXIT_CHILD_BINDING = r"""
+import sys, time
+from paper_1908_07341_gb300 import _lib
+so = _lib.lib()
+for k in range(3):
+    assert so.shk_specialize_prepare(_lib.BITPACK, 0, 0.7 + 0.01 * k, 0.3, 0) == 0
+time.sleep(float(sys.argv[1]))
+print("exiting", flush=True)
+"""
+
+
 @pytest.mark.parametrize("delay", [0.0, 0.15, 0.4, 0.8])
 def test_exit_during_a_background_compile_is_clean(delay):
     """A process that exits while compiles are queued or running waits for
     the one in flight and exits normally (no crash or hang in NVRTC's exit
-    handlers)."""
+    handlers): through the C exit handler (plain ctypes), and through the
+    binding's interpreter-exit hook."""
     _nvrtc()
-    lib_path = _lib.LIB_PATH
-    r = subprocess.run([sys.executable, "-c", _EXIT_CHILD, lib_path, str(delay)], capture_output=True,
+    r = subprocess.run([sys.executable, "-c", _EXIT_CHILD, _lib.LIB_PATH, str(delay)], capture_output=True,
                        text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     assert "exiting" in r.stdout
+    r = subprocess.run([sys.executable, "-c", _EXIT_CHILD_BINDING, str(delay)], capture_output=True, text=True,
+                       timeout=120, cwd=ROOT)
+    assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
+    assert "exiting" in r.stdout
+
+
+def test_shutdown_stops_background_compiles():
+    _nvrtc()
+    child = r"""
+import ctypes, sys
+so = ctypes.CDLL(sys.argv[1])
+so.shk_specialize_prepare.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+assert so.shk_specialize_prepare(1, 0, 0.61, 0.3, 0) == 0      # first compile: on this thread
+assert so.shk_specialize_prepare(1, 0, 0.62, 0.3, 0) == 0      # background
+assert so.shk_specialize_shutdown() == 0                        # waits for it
+assert so.shk_specialize_shutdown() == 0                        # idempotent
+c, f, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+so.shk_specialize_status(ctypes.byref(c), ctypes.byref(f), ctypes.byref(q), None, None, 0)
+assert q.value <= 1 and f.value == 0, (c.value, f.value, q.value)
+assert so.shk_specialize_prepare(1, 0, 0.63, 0.3, 0) != 0      # nothing new after shutdown
+print("ok", c.value, q.value)
+"""
+    r = subprocess.run([sys.executable, "-c", child, _lib.LIB_PATH], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "ok" in r.stdout, (r.returncode, r.stdout, r.stderr[-2000:])
