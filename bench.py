@@ -768,7 +768,7 @@ def _kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("device.cuh", "bounds.cuh", "sweep.cuh", "sweep_kernels.cuh", "kernels.cu", "jit.cu"):  # the sweeps' sources
+    for f in ("device.cuh", "bounds.cuh", "sweep.cuh", "sweep_kernels.cuh"):   # the sweep kernels' device code
         with open(os.path.join(ROOT, "paper_1908_07341_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

@@ -372,8 +372,14 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
     if (g.layout == kBitpack || g.aligned) {
         const SweepVariant* table = g.layout == kBitpack ? kBpVariants : kI8Variants;
         int vi = g.layout == kBitpack ? g_bp_variant.load() : g_i8_variant.load();
+        const int fallback = g.layout == kBitpack ? kBpRowFallback : kI8RowFallback;
         // strip-walk and vector variants need rows of a multiple of their block count
-        if ((g.Wr % (uint32_t)table[vi].row_blocks) != 0) vi = g.layout == kBitpack ? kBpRowFallback : kI8RowFallback;
+        if ((g.Wr % (uint32_t)table[vi].row_blocks) != 0) vi = fallback;
+        // a vector variant (V blocks per thread) below one full wave of threads
+        // leaves SMs idle: the one-block-per-thread queue sweep is faster there
+        // (at L <= 2048 on a GB300)
+        const int rb = table[vi].row_blocks;
+        if (rb > 1 && rb < 32 && g.nblocks / (uint32_t)rb < (uint32_t)(sm_count() * 768)) vi = fallback;
         const SweepVariant& v = table[vi];
         cudaError_t e = cudaSuccess;
         if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e)) return e;

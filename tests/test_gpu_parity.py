@@ -252,7 +252,7 @@ def test_run_argument_errors():
 
 
 @pytest.mark.parametrize("layout,L", [("bitpack", 96), ("bitpack", 128), ("bitpack", 192), ("bitpack", 1024),
-                                      ("bitpack", 2048), ("int8", 64),
+                                      ("bitpack", 2048), ("bitpack", 4096), ("int8", 64),
                                       ("int8", 288), ("int8", 1024)])
 def test_every_sweep_variant_draws_the_same_spins(orc, layout, L):
     """The launch-shape variants the autotuner chooses from differ only in
