@@ -46,7 +46,7 @@ BUILD_DEBUG = os.path.join(PKG, "_build_debug")
 
 
 # The device headers that jit.cu compiles at run time, embedded as strings.
-JIT_SOURCES = ["device.cuh", "bounds.cuh", "sweep.cuh", "sweep_kernels.cuh"]
+JIT_SOURCES = ["device.cuh", "bounds.cuh", "sweep.cuh", "sweep_kernels.cuh", "checkerboard.cuh"]
 
 
 def _write_jit_sources(build_dir: str) -> None:

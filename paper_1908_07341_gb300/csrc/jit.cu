@@ -129,7 +129,7 @@ bool compile_cubin(JitEntry* en, std::string* log_out) {
         return false;
     }
     nvrtcProgram prog = nullptr;
-    const char* src = "#include \"sweep_kernels.cuh\"\n";
+    const char* src = "#include \"sweep_kernels.cuh\"\n#include \"checkerboard.cuh\"\n";
     if (n.create(&prog, src, "shk_jit.cu", kJitSourceCount, kJitSourceTexts, kJitSourceNames) != NVRTC_SUCCESS) {
         *log_out = "nvrtcCreateProgram failed";
         return false;

@@ -156,3 +156,30 @@ def test_exit_with_compiles_in_flight_is_clean():
                            cwd=root)
         assert r.returncode == 0, (r.returncode, r.stdout[-500:], r.stderr[-2000:])
         assert "exiting" in r.stdout
+
+
+@pytest.mark.parametrize("J", [0.44, 0.0, -0.3, 3.0])
+def test_specialised_checkerboard_matches_generic_and_oracle(orc, J):
+    """The checkerboard kernel compiled with the thresholds of J draws the
+    oracle's spins and sums, as the generic one does."""
+    from paper_1908_07341_gb300.lattice import checkerboard_run, pack_bits, unpack_bits
+    L, n = 96, 3
+    spins = random_spins(L, seed=13)
+    out = []
+    for mode in (2, 0):
+        _lib.lib().shk_set_specialize(mode)
+        try:
+            plane = shk.alloc_plane(L, "bitpack")
+            plane.zero_()
+            raw = pack_bits(spins).view(np.uint8)
+            plane[: raw.size].copy_(torch.from_numpy(raw.copy()))
+            rows = checkerboard_run(plane, L, J, 4, 2, 5, n).cpu().numpy()
+            out.append((unpack_bits(plane.cpu().numpy()[: L * L // 8], L).reshape(-1), rows))
+        finally:
+            _lib.lib().shk_set_specialize(1)
+    ref = spins.copy()
+    ref_rows = orc.checkerboard_run(ref, L, J, 4, 2, 5, n)
+    for got, rows in out:
+        assert np.array_equal(got, ref) and np.array_equal(rows, ref_rows)
+    c, f, log = _status()
+    assert f == 0, log

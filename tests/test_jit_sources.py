@@ -1,7 +1,8 @@
 """CPU checks of the run-time specialised sweeps: the embedded device headers
 compile under NVRTC for sm_103a with the three class thresholds as constants,
-for every sweep variant that names a specialised form, and the host-side
-controls behave (no GPU needed: compiling emits a cubin, nothing is launched).
+for every sweep variant that names a specialised form and for the
+checkerboard kernel, and the host-side controls behave (no GPU needed:
+compiling emits a cubin, nothing is launched).
 """
 import ctypes
 import os
@@ -48,8 +49,8 @@ def _compile(nv, names, U):
     prog = ctypes.c_void_p()
     hn = (ctypes.c_char_p * len(headers))(*[h.encode() for h in headers])
     ht = (ctypes.c_char_p * len(headers))(*texts)
-    assert nv.nvrtcCreateProgram(ctypes.byref(prog), b'#include "sweep_kernels.cuh"\n', b"shk_jit.cu",
-                                 len(headers), ht, hn) == 0
+    assert nv.nvrtcCreateProgram(ctypes.byref(prog), b'#include "sweep_kernels.cuh"\n#include "checkerboard.cuh"\n',
+                                 b"shk_jit.cu", len(headers), ht, hn) == 0
     for n in names:
         assert nv.nvrtcAddNameExpression(prog, n.encode()) == 0
     opts = [b"--gpu-architecture=sm_103a", b"-std=c++17"] + [f"-DSHK_JIT_U{i}={u}u".encode()
@@ -88,7 +89,7 @@ def test_embedded_sources_compile_under_nvrtc():
     T = (ctypes.c_uint32 * 6)()
     assert _lib.lib().shk_thresholds(0.5, 0.5, T) == _lib.OK
     U = [T[3], T[4], T[5]]
-    names = _name_expressions()
+    names = _name_expressions() + ["shk::k_checkerboard<0>", "shk::k_checkerboard<1>"]
     rc, log, lowered, cubin = _compile(nv, names, U)
     assert rc == 0, log
     assert cubin > 0
