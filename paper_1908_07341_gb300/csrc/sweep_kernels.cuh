@@ -589,15 +589,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
             if (i < nrows) {
                 const uint32_t r = row_at(i);
                 const size_t b = (size_t)r * W + col;
-                uint32_t* slot = ring[wib][i % DEPTH];
+                uint32_t* dst = &ring[wib][i % DEPTH][lane * NW];
                 if constexpr (LAYOUT == kBitpack) {
-                    cp_async4(slot + lane, checked(static_cast<const uint32_t*>(a.src), b, a.nblocks, SHK_SITE));
+                    cp_async4(dst, checked(static_cast<const uint32_t*>(a.src), b, a.nblocks, SHK_SITE));
                 } else {
-                    // the two 16-byte halves of each lane's 32 bytes go to two separate
-                    // 512-byte regions, so that 32 lanes read each half conflict-free
                     const uint4* q4 = reinterpret_cast<const uint4*>(a.src);
-                    cp_async16(slot + 4 * lane, checked(q4, 2 * b, 2 * (uint64_t)a.nblocks, SHK_SITE));
-                    cp_async16(slot + 128 + 4 * lane, checked(q4, 2 * b + 1, 2 * (uint64_t)a.nblocks, SHK_SITE));
+                    cp_async16(dst, checked(q4, 2 * b, 2 * (uint64_t)a.nblocks, SHK_SITE));
+                    cp_async16(dst + 4, checked(q4, 2 * b + 1, 2 * (uint64_t)a.nblocks, SHK_SITE));
                 }
                 if (edge_lane) {
                     const size_t eb = (size_t)r * W + edge_block;
@@ -624,13 +622,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
             const uint32_t row = row_at(i);
             cp_async_wait<DEPTH - 1>();      // row i has landed (this lane's copies)
             __syncwarp();                    // ... and every other lane's
-            const uint32_t* slot = ring[wib][i % DEPTH];
+            const uint32_t* slot = &ring[wib][i % DEPTH][lane * NW];
             uint32_t S;
             if constexpr (LAYOUT == kBitpack) {
-                S = slot[lane];
+                S = slot[0];
             } else {
-                const uint4 lo = *reinterpret_cast<const uint4*>(slot + 4 * lane);
-                const uint4 hi = *reinterpret_cast<const uint4*>(slot + 128 + 4 * lane);
+                const uint4 lo = *reinterpret_cast<const uint4*>(slot);
+                const uint4 hi = *reinterpret_cast<const uint4*>(slot + 4);
                 S = pack_up32(lo, hi);
             }
             uint32_t edge = 0;
