@@ -15,6 +15,7 @@
 // compile fails, the caller launches the generic kernel, which computes the
 // same spins and sums.
 #include <dlfcn.h>
+#include <pthread.h>
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -27,6 +28,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -200,6 +202,17 @@ void stop_worker() {
     if (t && t->joinable()) t->join();
 }
 
+// fork(): the child has no worker thread.  The parent holds g_mu across the
+// fork so that the child's copy is consistent; the child stops run-time
+// compilation (its requests run generic, and blocking waits return).
+void atfork_prepare() { g_mu.lock(); }
+void atfork_parent() { g_mu.unlock(); }
+void atfork_child() {
+    g_stop = true;
+    g_worker = nullptr;
+    g_mu.unlock();
+}
+
 // The entry of (e0, U), queued for compile when new.  force: queue even past
 // kMaxQueued.  Null when no entry can be made (stopping, too many entries,
 // queue full, no NVRTC).  Called with g_mu held.
@@ -212,7 +225,8 @@ JitEntry* find_or_queue(const char* e0, const char* e1, int block, const uint32_
         g_last_log = "NVRTC could not be loaded";
         return nullptr;
     }
-    JitEntry* en = new JitEntry;
+    JitEntry* en = new (std::nothrow) JitEntry;
+    if (en == nullptr) return nullptr;
     en->e[0] = e0;
     en->e[1] = e1;
     std::copy(U, U + 3, en->U);
@@ -231,7 +245,13 @@ JitEntry* find_or_queue(const char* e0, const char* e1, int block, const uint32_
         en->state = ok ? JitEntry::kCompiled : JitEntry::kFailed;
         if (!ok) g_last_log = log;
         std::atexit(stop_worker);
-        g_worker = new std::thread(worker_main);
+        pthread_atfork(atfork_prepare, atfork_parent, atfork_child);
+        try {
+            g_worker = new std::thread(worker_main);
+        } catch (...) {
+            g_stop = true;          // no background compiles: tables not yet compiled run generic
+            g_last_log = "could not start the compile thread";
+        }
         return en;
     }
     g_queue.push_back(en);

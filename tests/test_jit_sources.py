@@ -203,3 +203,27 @@ print("ok", c.value, q.value)
 """
     r = subprocess.run([sys.executable, "-c", child, _lib.LIB_PATH], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and "ok" in r.stdout, (r.returncode, r.stdout, r.stderr[-2000:])
+
+
+def test_forked_child_does_not_wait_for_compiles():
+    """A child forked after the compile thread started has no such thread: its
+    blocking requests return at once instead of waiting for ever."""
+    _nvrtc()
+    child = r"""
+import ctypes, os, sys
+so = ctypes.CDLL(sys.argv[1])
+so.shk_specialize_prepare.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+assert so.shk_specialize_prepare(1, 0, 0.71, 0.3, 1) == 0      # first compile, starts the thread
+assert so.shk_specialize_prepare(1, 0, 0.72, 0.3, 0) == 0      # queued in the background
+pid = os.fork()
+if pid == 0:
+    rc = so.shk_specialize_prepare(1, 0, 0.73, 0.3, 1)         # must not block
+    os._exit(0 if rc != 0 else 3)
+_, status = os.waitpid(pid, 0)
+assert os.WIFEXITED(status) and os.WEXITSTATUS(status) == 0, status
+assert so.shk_specialize_prepare(1, 0, 0.74, 0.3, 1) == 0      # the parent still compiles
+print("ok")
+"""
+    r = subprocess.run([sys.executable, "-W", "ignore", "-c", child, _lib.LIB_PATH], capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0 and "ok" in r.stdout, (r.returncode, r.stdout, r.stderr[-2000:])
