@@ -150,14 +150,32 @@ def test_config_1024_bitpack(orc):
 
 
 @pytest.mark.parametrize("layout", ["bitpack", "int8"])
-def test_config_16384_sampled(orc, layout):
+@pytest.mark.parametrize("specialize", [2, 0])
+def test_config_16384_sampled(orc, layout, specialize):
     """16384x16384 (2.7e8 sites per sublattice), random start, q=1.0, J=0.35,
-    seed 3, in the launch configuration of the benchmark: steps t = 2 and
-    t = 1999 (the 2000th) are checked on sampled row bands, including both
-    wrap-around rows, recomputed by the oracle from the GPU's state at t-1;
-    the step's five sums are checked against the oracle on the whole plane."""
+    seed 3, in the launch configuration of the benchmark (the default sweep
+    variant, compiled with the thresholds as constants; and, for comparison,
+    the generic kernel): steps t = 2 and t = 1999 (the 2000th) are checked on
+    sampled row bands, including both wrap-around rows, recomputed by the
+    oracle from the GPU's state at t-1; the step's five sums are checked
+    against the oracle on the whole plane."""
+    from paper_1908_07341_gb300 import tune
     L, q, J, seed = 16384, 1.0, 0.35, 3
     T = orc.thresholds(q, J)
+    before = tune.get_variant(layout)
+    tune.set_variant(layout, 0)
+    shk.specialize(specialize)
+    try:
+        _check_16384(orc, layout, L, q, J, seed, T)
+        if specialize:
+            st = shk.specialize_status()
+            assert st["failed"] == 0 and st["compiled"] >= 1, st
+    finally:
+        shk.specialize(1)
+        tune.set_variant(layout, before)
+
+
+def _check_16384(orc, layout, L, q, J, seed, T):
     lat = shk.Lattice(L, layout).set_seed(seed, 0).set_params(q, J).init("random", init_seed=3)
     bands = [(0, 3), (5000, 5003), (16381, 16384)]
     for target in (2, 1999):
