@@ -176,6 +176,7 @@ __device__ __forceinline__ void cb_drain(const SweepArgs& a, uint32_t* pl, uint3
 
 template <int PARITY>
 __global__ void __launch_bounds__(256, 3) k_checkerboard(const SweepArgs a) {
+    pdl_begin();
     __shared__ uint32_t qbuf[8][6][kQueueCap];
     uint32_t* pl = static_cast<uint32_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;

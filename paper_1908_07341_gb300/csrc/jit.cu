@@ -342,7 +342,17 @@ bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t wo
     const uint64_t need = ((uint64_t)work_items + block - 1) / block;
     const int grid = (int)std::max<uint64_t>(1, std::min(full, need));
     void* args[] = {const_cast<SweepArgs*>(&a)};
-    *err = cudaLaunchKernel(reinterpret_cast<const void*>(l->k[half]), dim3(grid), dim3(block), args, 0, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // as launch_pdl
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    *err = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void*>(l->k[half]), args);
     return true;
 #endif
 }

@@ -285,7 +285,6 @@ SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawPa
 // Launch shapes of the half-step sweeps, chosen per layout at run time
 // (shk_set_sweep_variant; the autotuner times them and picks one).
 
-using SweepKernel = void (*)(SweepArgs);
 
 struct SweepVariant {
     SweepKernel k[2];   // half A, half B
@@ -384,15 +383,11 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
         cudaError_t e = cudaSuccess;
         if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e)) return e;
         SweepKernel k = v.k[half];
-        const int grid = grid_for(k, v.block, g.nblocks);
-        k<<<grid, v.block, 0, st>>>(a);
+        return launch_pdl(k, grid_for(k, v.block, g.nblocks), v.block, st, a);
     } else {
         const int block = 256;
-        if (half == 0) {
-            k_sweep_i8g<0><<<grid_for(k_sweep_i8g<0>, block, g.nblocks), block, 0, st>>>(a);
-        } else {
-            k_sweep_i8g<1><<<grid_for(k_sweep_i8g<1>, block, g.nblocks), block, 0, st>>>(a);
-        }
+        SweepKernel k = half == 0 ? k_sweep_i8g<0> : k_sweep_i8g<1>;
+        return launch_pdl(k, grid_for(k, block, g.nblocks), block, st, a);
     }
     return cudaGetLastError();
 }
@@ -401,14 +396,8 @@ cudaError_t launch_cnn(const Geometry& g, const void* sigma, long long* obs, cud
     DrawParams P{};
     const SweepArgs a = sweep_args(g, sigma, nullptr, P, 0, obs, nullptr, nullptr);
     const int block = 256;
-    if (g.layout == kBitpack) {
-        k_cnn<kBitpack, true><<<grid_for(k_cnn<kBitpack, true>, block, g.nblocks), block, 0, st>>>(a);
-    } else if (g.aligned) {
-        k_cnn<kInt8, true><<<grid_for(k_cnn<kInt8, true>, block, g.nblocks), block, 0, st>>>(a);
-    } else {
-        k_cnn<kInt8, false><<<grid_for(k_cnn<kInt8, false>, block, g.nblocks), block, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    SweepKernel k = g.layout == kBitpack ? k_cnn<kBitpack, true> : g.aligned ? k_cnn<kInt8, true> : k_cnn<kInt8, false>;
+    return launch_pdl(k, grid_for(k, block, g.nblocks), block, st, a);
 }
 
 cudaError_t launch_init(const Geometry& g, void* plane, int kind, uint64_t init_seed,

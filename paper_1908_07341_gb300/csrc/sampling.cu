@@ -386,12 +386,8 @@ cudaError_t launch_checkerboard(const Geometry& g, void* plane, const DrawParams
     cudaError_t e = cudaSuccess;
     if (jit_launch("shk::k_checkerboard<0>", "shk::k_checkerboard<1>", block, parity, (uint32_t)draw_blocks, a, st, &e))
         return e;
-    if (parity == 0) {
-        k_checkerboard<0><<<grid_for(k_checkerboard<0>, block, draw_blocks), block, 0, st>>>(a);
-    } else {
-        k_checkerboard<1><<<grid_for(k_checkerboard<1>, block, draw_blocks), block, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    SweepKernel k = parity == 0 ? k_checkerboard<0> : k_checkerboard<1>;
+    return launch_pdl(k, grid_for(k, block, draw_blocks), block, st, a);
 }
 
 unsigned bounds_site_sampling() { return take_bounds_site(); }

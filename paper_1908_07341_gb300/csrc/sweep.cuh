@@ -31,6 +31,16 @@ struct SweepArgs {
     PhiloxPrefix pre[8];  // round prefixes of the 8 Philox calls of half-step hs
 };
 
+// Programmatic dependent launch: the kernels are launched so that the next
+// kernel in the stream may be scheduled while this one still runs.  Each waits
+// here until the kernel before it has completed and its writes are visible
+// (nothing is read or written before), then lets the next one be scheduled.
+// Both are no-ops for a launch that did not ask for it.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------ neighbour gathers
 
 // Bits of block w of a bit-packed (or bit-converted) plane and of the two field
@@ -139,6 +149,25 @@ int sm_count();
 int blocks_per_sm(const void* kernel, int block);
 SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawParams& P,
                      uint32_t hs, long long* oc, long long* op, long long* z);
+
+using SweepKernel = void (*)(SweepArgs);
+
+// Launches kernel(a) with programmatic stream serialization (see pdl_begin):
+// its launch overlaps the tail of the kernel before it in the stream.
+template <class K>
+inline cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t st, const SweepArgs& a) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
 
 // Grid of at most one full wave of resident blocks (the kernels stride over
 // their work), never more blocks than work items need.

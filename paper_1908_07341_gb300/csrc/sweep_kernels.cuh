@@ -81,6 +81,7 @@ __device__ __forceinline__ void decode_bp(const RawBp& r, uint32_t& S, uint32_t&
 // PREFETCH, issues the loads of its next group before drawing the current one.
 template <int HALF, int ILP, bool PREFETCH, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_bp(const SweepArgs a) {
+    pdl_begin();
     const uint32_t* __restrict__ src = static_cast<const uint32_t*>(a.src);
     uint32_t* __restrict__ dst = static_cast<uint32_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;
@@ -165,6 +166,7 @@ __device__ __forceinline__ void decode_i8(const RawI8& r, uint32_t& S, uint32_t&
 // the walk, optionally prefetching the next block's bytes).
 template <int HALF, bool PREFETCH, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_i8a(const SweepArgs a) {
+    pdl_begin();
     const int8_t* __restrict__ src = static_cast<const int8_t*>(a.src);
     int8_t* __restrict__ dst = static_cast<int8_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;
@@ -240,6 +242,7 @@ __device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, uin
 
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
+    pdl_begin();
     __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
     const DrawParams& P = a.P;
     const uint32_t lane = threadIdx.x & 31;
@@ -322,6 +325,7 @@ __device__ __forceinline__ void load_words(const uint32_t* __restrict__ pl, uint
 // the number of vectors a multiple of 32: every lane is active.
 template <int HALF, int V, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_qv(const SweepArgs a) {
+    pdl_begin();
     __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
     const DrawParams& P = a.P;
     const uint32_t* __restrict__ src = static_cast<const uint32_t*>(a.src);
@@ -451,6 +455,7 @@ __device__ __forceinline__ uint32_t edge_bit(const void* src, uint32_t row, uint
 
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) {
+    pdl_begin();
     __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -553,6 +558,7 @@ struct RowWords {
 
 template <int HALF, int LAYOUT, int BLOCK, int MINB, int DEPTH>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepArgs a) {
+    pdl_begin();
     constexpr int NW = RowWords<LAYOUT>::kWords;
     __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
     const DrawParams& P = a.P;
@@ -688,6 +694,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
 // int8 half-step for any L (site-by-site neighbour gathers; partial last block).
 template <int HALF>
 __global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {
+    pdl_begin();
     const int8_t* __restrict__ src = static_cast<const int8_t*>(a.src);
     int8_t* __restrict__ dst = static_cast<int8_t*>(a.dst);
     const uint32_t lane = threadIdx.x & 31;
@@ -716,6 +723,7 @@ __global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {
 // the torus to sum sigma_x (sigma_{x up} + sigma_{x right}); added to obs_cur[4].
 template <int LAYOUT, bool ALIGNED>
 __global__ void __launch_bounds__(256) k_cnn(const SweepArgs a) {
+    pdl_begin();
     int acc = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
     for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < a.nblocks; w += stride) {
