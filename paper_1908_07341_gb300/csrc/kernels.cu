@@ -427,9 +427,11 @@ static uint32_t small_block_threads(const Geometry& g) {
 }
 
 bool small_path_fits(const Geometry& g) {
-    // Lattices up to 2^16 sites per plane (L <= 256) run faster inside one CTA
-    // than as a sequence of grid-wide launches.
-    return g.N <= 65536;
+    // Lattices up to 2^15 sites per plane (L <= 181) run faster inside one CTA
+    // than as a sequence of grid-wide launches: on a GB300 a step takes 2.6 us
+    // at L = 128 in one CTA, 8.3 us at L = 256, against about 5 us on the grid
+    // path (whose launches overlap, see pdl_begin) from L = 256 to 1024.
+    return g.N <= 32768;
 }
 
 cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const DrawParams& P,
