@@ -465,11 +465,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     }
     if not args.no_batched:
         line["batched"] = bench_batched(dev, stream)
-    if not args.no_serving:
-        line["serving"] = bench_serving(dev, stream, n_jobs=args.serving_jobs)
     if not args.no_section3:
         line["section3"] = bench_section3(dev, stream)
         line["l_sweep"] = bench_l_sweep(dev, stream)
+    if not args.no_serving:      # last: the longest leg, which heats the GPU most
+        line["serving"] = bench_serving(dev, stream, n_jobs=args.serving_jobs)
     if world == 1 and not args.no_cpu_baseline:
         rate, secs, units, cores = _oracle_rate_all_cores(steps=4, warmup=1)
         line["cpu_baseline"] = {
