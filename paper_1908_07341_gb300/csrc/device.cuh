@@ -335,10 +335,15 @@ __device__ __forceinline__ uint32_t pack_up4(uint32_t x) {
     return (((~x) & 0x80808080u) * 0x00204081u) >> 28;
 }
 
+// Up-bits of 32 int8 spins (bytes of lo, then hi): the four flags of each
+// word land in bits 28..31 of its product, and a funnel shift appends them to
+// the result, last word first, so that word m ends in bits 4m..4m+3.
 __device__ __forceinline__ uint32_t pack_up32(const uint4& lo, const uint4& hi) {
-    return pack_up4(lo.x) | (pack_up4(lo.y) << 4) | (pack_up4(lo.z) << 8) |
-           (pack_up4(lo.w) << 12) | (pack_up4(hi.x) << 16) | (pack_up4(hi.y) << 20) |
-           (pack_up4(hi.z) << 24) | (pack_up4(hi.w) << 28);
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    uint32_t acc = 0;
+#pragma unroll
+    for (int m = 7; m >= 0; --m) acc = __funnelshift_l(((~w[m]) & 0x80808080u) * 0x00204081u, acc, 4);
+    return acc;
 }
 
 // Four int8 spins from the low four bits of nib (bit k -> byte k).
