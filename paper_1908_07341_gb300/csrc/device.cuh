@@ -346,10 +346,15 @@ __device__ __forceinline__ uint32_t pack_up32(const uint4& lo, const uint4& hi) 
     return acc;
 }
 
-// Four int8 spins from the low four bits of nib (bit k -> byte k).
+// Four int8 spins from the low four bits of nib (bit k -> byte k): the
+// product puts bit k on the sign bit of byte k (nib < 16, so the partial
+// products do not overlap there), prmt replicates each byte's sign bit over
+// the byte, and the complement with bit 0 set gives +1 = 0x01, -1 = 0xFF.
 __device__ __forceinline__ uint32_t unpack4(uint32_t nib) {
-    const uint32_t y = (nib * 0x00204081u) & 0x01010101u;
-    return ~(y * 0xFEu);
+    const uint32_t s = nib * 0x10204080u;
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(s));
+    return ~r | 0x01010101u;
 }
 
 __device__ __forceinline__ void unpack32(uint32_t bits, uint4& lo, uint4& hi) {
