@@ -463,11 +463,16 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                                 "launch's compiles (compile_s, host seconds) come before the warm-up "
                                 "steps"},
     }
+    def spec_status():
+        return {k: v for k, v in shk.specialize_status().items() if k != "log"}
+
     if not args.no_batched:
         line["batched"] = bench_batched(dev, stream)
+        line["specialized"]["after_batched"] = spec_status()
     if not args.no_section3:
         line["section3"] = bench_section3(dev, stream)
         line["l_sweep"] = bench_l_sweep(dev, stream)
+        line["specialized"]["after_section3"] = spec_status()
     if not args.no_serving:      # last: the longest leg, which heats the GPU most
         line["serving"] = bench_serving(dev, stream, n_jobs=args.serving_jobs)
     if world == 1 and not args.no_cpu_baseline:
@@ -511,7 +516,13 @@ def bench_batched(dev, stream, plain_steps: int = 100):
     stats = b.read_stats()
     assert int(stats[:, 10].min()) == w["steps"] - w["burn_in"]
     b.close()
-    # plain per-lattice launches of the same lattices on one stream
+    # plain per-lattice launches of the same lattices on one stream, in the
+    # library's default specialisation mode (compiles in the background, at
+    # most two queued): with one (q, J) table per lattice, blocking compiles
+    # would take minutes and fill the compile cache, so most of these
+    # lattices run the generic sweeps, as they would for a user
+    mode_before = shk.specialize()
+    shk.specialize(shk.lattice.SPECIALIZE_BACKGROUND)
     lats = []
     for i in range(len(L)):
         lat = shk.Lattice(int(L[i]), "bitpack", device=dev, stream=stream)
@@ -529,6 +540,8 @@ def bench_batched(dev, stream, plain_steps: int = 100):
     plain_ms = s.elapsed_time(e)
     for lat in lats:
         lat.close()
+    shk.wait_specialized()
+    shk.specialize(mode_before)
     batched_rate = units_per_step * w["steps"] / (batched_ms / 1e3)
     plain_rate = units_per_step * plain_steps / (plain_ms / 1e3)
     return {"workload": "1024 lattices, L log-uniform in {32..2048} (seeded), 32x32 (q,J) grid "

@@ -276,7 +276,8 @@ int shk_barrier_timeout_test(unsigned int spin_limit, uint32_t* dev_words, int* 
  * background thread, launches do not wait for it (at most 2 tables queued,
  * 512 per process; requests beyond these run generic), except for the
  * process's first compile, which runs on the calling thread; 2 compile at
- * first use and wait for it.  SHK_EINVAL for another mode; shk_get_specialize returns
+ * first use and wait for it (at most two minutes, then the generic kernel
+ * runs).  SHK_EINVAL for another mode; shk_get_specialize returns
  * the current one.  A compiled kernel is loaded at its first launch on a
  * stream that is not being captured into a CUDA graph (launches under capture
  * run generic until then).  shk_specialize_status
@@ -294,7 +295,8 @@ int shk_specialize_status(int* compiled, int* failed, int* queued, double* compi
  * also waits for the compile.  SHK_EINVAL for non-finite q or J, an unknown
  * variant or one without a specialised form; SHK_ESTATE when specialisation
  * is off, NVRTC cannot be loaded, the compile failed (wait != 0) or in the
- * bounds-checked build.  For callers that know their tables ahead of time. */
+ * bounds-checked build; SHK_ETIMEOUT when wait != 0 and the compile took
+ * longer than two minutes.  For callers that know their tables ahead of time. */
 int shk_specialize_prepare(int layout, int variant, double q, double J, int wait);
 /* Stops the background compiler: waits for the compile in flight, if any,
  * and queues no more (tables not yet compiled then run generic).  Idempotent.

@@ -120,6 +120,7 @@ double g_compile_s = 0.0;                 // host seconds spent compiling, all e
 
 constexpr size_t kMaxQueued = 2;          // launches queue no table beyond this (generic kernel meanwhile)
 constexpr size_t kMaxEntries = 512;       // bound on compiled tables per process
+constexpr std::chrono::seconds kWaitLimit(120);   // longest blocking wait for one compile
 
 // NVRTC compile of the entry's two kernels with its thresholds as
 // constants; fills cubin and the lowered names, or returns false with the
@@ -323,7 +324,8 @@ bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t wo
         std::unique_lock<std::mutex> lock(g_mu);
         JitEntry* en = find_or_queue(e0, e1, block, U, mode == 2);
         if (en == nullptr) return false;
-        if (mode == 2) g_cv.wait(lock, [en] { return en->state != JitEntry::kQueued || g_stop; });
+        // blocking mode waits for the compile, at most kWaitLimit (the generic kernel runs after that)
+        if (mode == 2) g_cv.wait_for(lock, kWaitLimit, [en] { return en->state != JitEntry::kQueued || g_stop; });
         if (en->state != JitEntry::kCompiled) return false;
         if (en->dev.find(dev) == en->dev.end()) {
             // loading a module is not allowed while the stream is being
@@ -388,7 +390,10 @@ int jit_prepare(int layout, int variant, const uint32_t T[6], bool wait, std::st
         return SHK_ESTATE;
     }
     if (!wait) return SHK_OK;
-    g_cv.wait(lock, [en] { return en->state != JitEntry::kQueued || g_stop; });
+    if (!g_cv.wait_for(lock, kWaitLimit, [en] { return en->state != JitEntry::kQueued || g_stop; })) {
+        *why = "the compile did not finish within the wait limit";
+        return SHK_ETIMEOUT;
+    }
     if (en->state != JitEntry::kCompiled) {
         *why = g_last_log.empty() ? std::string("the compile did not finish") : g_last_log;
         return SHK_ESTATE;
