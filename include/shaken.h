@@ -159,6 +159,10 @@ int shk_halfstep(int layout, int half, const void* src, void* dst, int L,
  * variant draws the same spins -- only the speed.  The setting is
  * process-wide and applies to launches enqueued after the call; the autotuner
  * (paper_1908_07341_gb300.tune) times the variants and sets the fastest.
+ * A variant whose shape does not fit the lattice (rows of fewer blocks than
+ * it walks or loads at once, or, for the vector variants, fewer blocks than
+ * one full wave of threads needs) falls back to the one-block-per-thread
+ * queue sweep for that launch.
  * The paper has no counterpart (it is a property of this implementation).
  * shk_sweep_variant_name returns NULL for an unknown (layout, variant);
  * shk_set_sweep_variant returns SHK_EINVAL for one. */
