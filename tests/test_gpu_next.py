@@ -76,6 +76,31 @@ def test_checkerboard_run_matches_oracle(orc, L, J, n):
     assert np.array_equal(got_obs, ref_obs)
 
 
+def test_checkerboard_16384_full_plane_against_oracle(orc):
+    """The benchmark's checkerboard workload (16384^2, J = 0.44, seed 3, random
+    start) in the benchmark's launch configuration (specialised kernels):
+    after 6 GPU steps, step t = 6 is recomputed by the oracle from the GPU's
+    state over the whole plane and both (M, C_nn) sums compared; then the
+    benchmark's diagonal sums (lags 1..16) of that plane."""
+    L, J, seed = 16384, 0.44, 3
+    shk.specialize(2)
+    try:
+        plane = shk.alloc_plane(L, "bitpack")
+        shk.init_plane("bitpack", plane, L, "random", init_seed=3)
+        checkerboard_run(plane, L, J, seed, 0, 0, 6, obs=False)
+        ref = from_device_plane(plane, L, "bitpack")
+        rows = checkerboard_run(plane, L, J, seed, 0, 6, 1).cpu().numpy()
+        ref_rows = orc.checkerboard_run(ref, L, J, seed, 0, 6, 1)
+        assert np.array_equal(rows, ref_rows)
+        assert np.array_equal(from_device_plane(plane, L, "bitpack"), ref)
+        assert shk.specialize_status()["failed"] == 0
+        # the benchmark's diagonal sums on the same plane
+        lags = [1, 2, 4, 8, 16]
+        assert np.array_equal(diag_correlations(plane, L, lags).cpu().numpy(), orc.diag_correlations(ref, L, lags))
+    finally:
+        shk.specialize(1)
+
+
 def test_checkerboard_resume_and_lattice_ids(orc):
     L = 64
     s = random_spins(L, seed=5, p_up=0.5)
