@@ -250,22 +250,6 @@ int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const dou
  * the measured Philox ceiling of the bit-packed draw.  Asynchronous. */
 int shk_philox_peak(int blocks, uint32_t iters, uint32_t* dev_out, void* stream);
 
-/* The one-launch path of shk_run: with it enabled, a bit-packed lattice with
- * L^2 > 65536 and L <= 4096 runs all n steps in a single cooperative launch, a bounded grid
- * barrier between the half-steps (same spins and sums as the per-launch
- * path).  If a barrier gives up (it polls at most about two seconds), the
- * next shk_read_observables / shk_read_spins on the handle returns
- * SHK_ETIMEOUT.  shk_set_one_launch(1) enables the path, process-wide; it is
- * off by default because on a GB300 it measured no faster than the
- * per-launch path (both 8 to 20 us per step for L = 288 .. 4096), while it
- * issues one launch per run instead of 2n + 1 (less host work).
- * shk_barrier_timeout_test launches the barrier with an arrival count that
- * can never complete and reports in *timed_out whether both waiting CTAs gave
- * up after spin_limit polls (1..2^20); dev_words: 3 device uint32.
- * Synchronous.  It exists to test the failure path without a fault. */
-int shk_set_one_launch(int enabled);
-int shk_barrier_timeout_test(unsigned int spin_limit, uint32_t* dev_words, int* timed_out, void* stream);
-
 /* Run-time specialisation of the half-step sweeps (no counterpart in the
  * paper).  The draw of Eqs. leftTrans / rightTrans compares the random bit
  * planes with the bits of the three class thresholds of (q, J); compiled with
@@ -314,7 +298,7 @@ int shk_specialize_shutdown(void);
 typedef struct shk_lattice shk_lattice;
 
 /* Device bytes a lattice of side L needs: both planes plus 512 bytes of
- * observable ring and barrier words.  0 if (L, layout) is invalid. */
+ * observable ring (256 of them reserved).  0 if (L, layout) is invalid. */
 size_t shk_lattice_bytes(int L, int layout);
 
 /* Creates a handle over caller-owned device memory dev_mem (at least
@@ -495,9 +479,10 @@ int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes);
  * chain (the sigma-marginal of the alternate dynamics) in place on the
  * caller's sigma plane, and gives the same spins and sums as shk_run on a
  * handle holding that sigma.
- *   sigma     device plane of shk_plane_bytes(L, layout) bytes (input and output).
- *   last_obs  nullable device array of SHK_NOBS int64: the five sums of the
- *             last step (sigma, tau at its end).
+ *   sigma     device plane of shk_plane_bytes(L, layout) bytes (input and
+ *             output), 16-byte aligned (the sweeps use 16-byte vector loads).
+ *   last_obs  nullable device array of SHK_NOBS int64, 8-byte aligned: the
+ *             five sums of the last step (sigma, tau at its end).
  *   stream    cudaStream_t as void*; the device that is current at the call
  *             is the one used.
  * The call allocates nothing and calls no allocating routine.  The transient
@@ -506,10 +491,15 @@ int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes);
  * until the process exits.  The array keeps the last call's contents;
  * accumulators are cleared at the start of every call.  Calls whose GPU work
  * overlaps (different streams or host threads) share the array and race.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); make the first call on a device before any stream
+ * capture.  The call never compiles or loads a run-time specialised sweep
+ * (loading a module allocates): it uses one only if an earlier call of the
+ * library already loaded it on this device, and the generic sweep otherwise,
+ * with the same spins and sums.
  * Errors: SHK_EINVAL for sizes beyond the scratch (message says the limit),
- * bad L/layout, non-finite q or J, or a step index reaching SHK_MAX_STEP;
+ * bad L/layout, a NULL or misaligned sigma, a misaligned last_obs, non-finite
+ * q or J, or a step index reaching SHK_MAX_STEP (all before any launch);
  * SHK_ECUDA if a launch fails.  Messages via shk_last_error(NULL). */
 int shk_shaken_run_static(int layout, void* sigma, int L, double q, double J, uint64_t seed,
                           uint32_t lattice_id, uint64_t t0, uint64_t n_steps, int64_t* last_obs,

@@ -50,13 +50,11 @@ SIGNATURES = {
     "shk_cftp_scratch_bytes": (_sz, [_i]),
     "shk_philox_peak": (_i, [_i, _u32, _vp, _vp]),
     "shk_debug_bounds": (_i, [_vp]),
-    "shk_set_one_launch": (_i, [_i]),
     "shk_set_specialize": (_i, [_i]),
     "shk_get_specialize": (_i, []),
     "shk_specialize_prepare": (_i, [_i, _i, _d, _d, _i]),
     "shk_specialize_shutdown": (_i, []),
     "shk_specialize_status": (_i, [_vp, _vp, _vp, _vp, _vp, _sz]),
-    "shk_barrier_timeout_test": (_i, [_u32, _vp, _vp, _vp]),
     "shk_cftp": (_i, [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _vp, _sz, _vp, _sz, _vp, _vp]),
     "shk_checkerboard_thresholds": (_i, [_d, _vp]),
     "shk_checkerboard_run": (_i, [_vp, _i, _d, _u64, _u32, _u64, _u64, _vp, _vp]),

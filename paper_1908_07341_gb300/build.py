@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libshaken.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "peak.cu", "sampling.cu", "coop.cu", "jit.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "batch.cu", "peak.cu", "sampling.cu", "jit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

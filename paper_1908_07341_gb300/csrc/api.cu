@@ -102,7 +102,6 @@ struct shk_lattice {
     size_t bytes = 0;
     void* plane[2] = {nullptr, nullptr};
     long long* ring = nullptr;      // 4 slots x 8 int64
-    unsigned int* bar = nullptr;    // arrivals, generation, timeout flag of the one-launch path
     long long* last_obs = nullptr;  // device row of the last completed step
     cudaStream_t stream = nullptr;
     double q = 0.0, J = 0.0;
@@ -111,7 +110,6 @@ struct shk_lattice {
     uint64_t seed = 0;
     uint32_t lattice_id = 0;
     uint64_t step = 0;
-    bool coop_ran = false;          // a one-launch run is in flight or done: check its barrier flag
     std::string err;
 };
 
@@ -134,25 +132,7 @@ int cuda_fail(shk_lattice* lat, cudaError_t e, const char* what) {
     return fail(lat, SHK_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-constexpr size_t kRingBytes = 512;   // 4 observable slots of 8 int64, then the grid-barrier words
-constexpr unsigned int kCoopSpinLimit = 1u << 24;   // barrier polls (a 64 ns pause each after the first 1024)
-// Off by default: on a GB300 the one-launch path measured no faster than the
-// per-launch path (8 to 20 us per step either way for L = 288 .. 4096); it
-// issues one launch per run instead of 2n + 1.
-std::atomic<bool> g_coop_enabled{false};
-
-// After a one-launch run: SHK_ETIMEOUT if one of its grid barriers gave up
-// (its spins and sums are then incomplete).  The stream must be synchronised.
-int coop_status(shk_lattice* lat) {
-    if (!lat->coop_ran) return SHK_OK;
-    unsigned int flag = 0;
-    cudaError_t e = cudaMemcpyAsync(&flag, lat->bar + 2, sizeof flag, cudaMemcpyDeviceToHost, lat->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
-    if (e != cudaSuccess) return cuda_fail(lat, e, "reading the grid-barrier flag");
-    if (flag != 0u)
-        return fail(lat, SHK_ETIMEOUT, "a grid barrier of the one-launch run gave up; the state is incomplete");
-    return SHK_OK;
-}
+constexpr size_t kRingBytes = 512;   // 4 observable slots of 8 int64, then 256 reserved bytes
 
 }  // namespace
 
@@ -186,8 +166,7 @@ int shk_debug_bounds(uint32_t* first_site) {
     *first_site = 0;
     if (!kBoundsChecked)
         return fail(nullptr, SHK_ESTATE, "shk_debug_bounds: the library was built without bounds checks");
-    const unsigned sites[4] = {bounds_site_kernels(), bounds_site_batch(), bounds_site_sampling(),
-                               bounds_site_coop()};
+    const unsigned sites[3] = {bounds_site_kernels(), bounds_site_batch(), bounds_site_sampling()};
     for (unsigned v : sites)
         if (v != 0 && *first_site == 0) *first_site = v;
     return SHK_OK;
@@ -206,8 +185,6 @@ size_t shk_plane_bytes(int L, int layout) {
 
 // Plane pointers of the stateless calls: the kernels read and write them in
 // 16-byte vectors.
-static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
 int shk_halfstep(int layout, int half, const void* src, void* dst, int L, const uint32_t T[6],
                  uint64_t seed, uint32_t lattice_id, uint32_t hs, int64_t* obs_accum,
                  void* stream) {
@@ -454,7 +431,6 @@ int shk_lattice_create(int L, int layout, void* dev_mem, size_t bytes, void* str
     lat->plane[0] = lat->dev;
     lat->plane[1] = lat->dev + g.plane_bytes;
     lat->ring = reinterpret_cast<long long*>(lat->dev + 2 * g.plane_bytes);
-    lat->bar = reinterpret_cast<unsigned int*>(lat->dev + 2 * g.plane_bytes + 256);
     lat->stream = static_cast<cudaStream_t>(stream);
     *out = lat;
     return SHK_OK;
@@ -524,25 +500,6 @@ int shk_run(shk_lattice* lat, uint64_t n_steps, int64_t* dev_obs) {
         e = launch_run_small(g, lat->plane[0], lat->plane[1], P, t0, n_steps, obs, lat->ring, st);
         if (e != cudaSuccess) return cuda_fail(lat, e, "shk_run (one-CTA path)");
         lat->last_obs = lat->ring;
-    } else if (g_coop_enabled && coop_path_fits(g) && n_steps <= 0xffffffffull) {
-        // one cooperative launch for all n steps (mid-size lattices)
-        e = obs ? cudaMemsetAsync(obs, 0, (size_t)kNumObs * sizeof(long long) * n_steps, st)
-                : cudaMemsetAsync(lat->ring + 8 * (t0 % 4), 0, (size_t)kNumObs * sizeof(long long), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(lat->bar, 0, 3 * sizeof(unsigned int), st);
-        if (e == cudaSuccess)
-            e = launch_run_coop(g, lat->plane[0], lat->plane[1], P, t0, n_steps, obs, lat->ring, lat->bar,
-                                kCoopSpinLimit, st);
-        if (e != cudaSuccess) return cuda_fail(lat, e, "shk_run (one-launch path)");
-        lat->coop_ran = true;
-        const uint64_t tl = t0 + n_steps - 1;
-        if (obs) {
-            e = cudaMemcpyAsync(lat->ring, obs + (size_t)kNumObs * (n_steps - 1), kNumObs * sizeof(long long),
-                                cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) return cuda_fail(lat, e, "shk_run copy of last row");
-            lat->last_obs = lat->ring;
-        } else {
-            lat->last_obs = lat->ring + 8 * (tl % 4);
-        }
     } else {
         auto slot = [&](uint64_t t) -> long long* {
             return obs ? obs + (size_t)kNumObs * (t - t0) : lat->ring + 8 * (t % 4);
@@ -582,7 +539,7 @@ int shk_read_observables(shk_lattice* lat, int64_t host_out[SHK_NOBS]) {
                                     cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(lat, e, "shk_read_observables");
-    return coop_status(lat);
+    return SHK_OK;
 }
 
 int shk_read_spins(shk_lattice* lat, int plane, int8_t* host_out) {
@@ -602,7 +559,7 @@ int shk_read_spins(shk_lattice* lat, int plane, int8_t* host_out) {
             for (int64_t u = 0; u < g.N; ++u) host_out[u] = ((words[u >> 5] >> (u & 31)) & 1u) ? 1 : -1;
     }
     if (e != cudaSuccess) return cuda_fail(lat, e, "shk_read_spins");
-    return coop_status(lat);
+    return SHK_OK;
 }
 
 int shk_write_spins(shk_lattice* lat, int plane, const int8_t* host_in) {
@@ -648,28 +605,6 @@ int shk_download_plane(shk_lattice* lat, int plane, void* host_raw, size_t bytes
     if (bytes < n) return fail(lat, SHK_ENOMEM, "shk_download_plane: %zu bytes given, %zu needed", bytes, n);
     const cudaError_t e = cudaMemcpyAsync(host_raw, lat->plane[plane], n, cudaMemcpyDeviceToHost, lat->stream);
     if (e != cudaSuccess) return cuda_fail(lat, e, "shk_download_plane");
-    return SHK_OK;
-}
-
-int shk_set_one_launch(int enabled) {
-    g_coop_enabled.store(enabled != 0);
-    return SHK_OK;
-}
-
-int shk_barrier_timeout_test(unsigned int spin_limit, uint32_t* dev_words, int* timed_out, void* stream) {
-    if (dev_words == nullptr || timed_out == nullptr || spin_limit == 0 || spin_limit > (1u << 20))
-        return fail(nullptr, SHK_EINVAL, "shk_barrier_timeout_test: bad argument (spin_limit in 1..2^20)");
-    *timed_out = 0;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // arrivals start past the last one, so the barrier can never open
-    const uint32_t init[3] = {2u, 0u, 0u};
-    cudaError_t e = cudaMemcpyAsync(dev_words, init, sizeof init, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_barrier_probe(dev_words, spin_limit, st);
-    uint32_t out[3] = {0u, 0u, 0u};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dev_words, sizeof out, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_barrier_timeout_test");
-    *timed_out = out[2] != 0u ? 1 : 0;
     return SHK_OK;
 }
 

@@ -39,9 +39,13 @@ bool make_draw_params(uint64_t seed, uint32_t lattice_id, const uint32_t T[6], u
 // plane (A: M_tau at [1]; B: M_sigma [0], S_q [2], S_J [3]); obs_prev (A only,
 // nullable) receives C_nn of the source plane at [4]; zero_slot (nullable)
 // is cleared by the launch (five int64).
+// loaded_only: launch a run-time specialised sweep only if it is already
+// compiled and loaded on this device; never queue a compile, compile, load a
+// module or wait (the allocation-free entry point), else the generic kernel.
 cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* dst,
                             const DrawParams& P, uint32_t hs, long long* obs_cur,
-                            long long* obs_prev, long long* zero_slot, cudaStream_t st);
+                            long long* obs_prev, long long* zero_slot, cudaStream_t st,
+                            bool loaded_only = false);
 
 // Launch-shape variants of the half-step sweeps (per layout; the int8 table
 // applies to L % 32 == 0).  The choice is process-wide.
@@ -85,19 +89,15 @@ cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const Dr
                              uint64_t t0, uint64_t n, long long* obs, long long* last,
                              cudaStream_t st);
 
+// True when p is 16-byte aligned (the sweeps use 16-byte vector accesses).
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
 // Number of SMs of the current device (cached).
 int sm_count();
 
 // Message returned by shk_last_error(NULL) on this host thread.
 void set_thread_error(const char* msg);
-
-// One cooperative launch for a whole run of a mid-size bit-packed lattice
-// (coop.cu); bar: 3 zeroed device words (arrivals, generation, timeout flag).
-bool coop_path_fits(const Geometry& g);
-cudaError_t launch_run_coop(const Geometry& g, void* sigma, void* tau, const DrawParams& P, uint64_t t0,
-                            uint64_t n, long long* obs, long long* ring, unsigned int* bar,
-                            unsigned int spin_limit, cudaStream_t st);
-cudaError_t launch_barrier_probe(unsigned int* bar, unsigned int spin_limit, cudaStream_t st);
 
 // Half-step sweeps compiled at run time for one threshold table (jit.cu).
 // jit_launch launches half `half` of the kernel pair named e0 / e1 and
@@ -107,7 +107,7 @@ cudaError_t launch_barrier_probe(unsigned int* bar, unsigned int spin_limit, cud
 // (default), 2 compile at first use and wait for it.
 struct SweepArgs;
 bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t work_items, const SweepArgs& a,
-                cudaStream_t st, cudaError_t* err);
+                cudaStream_t st, cudaError_t* err, bool loaded_only = false);
 extern std::atomic<int> g_jit_mode;
 // Queues (wait: and waits for) the specialised compile of sweep variant
 // `variant` of `layout` for threshold table T; SHK_OK or an error status with
@@ -122,7 +122,6 @@ bool sweep_variant_jit(int layout, int variant, const char** e0, const char** e1
 unsigned bounds_site_kernels();
 unsigned bounds_site_batch();
 unsigned bounds_site_sampling();
-unsigned bounds_site_coop();
 
 // Named range on the host timeline for profilers that record NVTX (no-op
 // when no tool is attached).

@@ -305,9 +305,9 @@ static void thresholds_of(const DrawParams& P, uint32_t U[3]) {
 // the caller launches the generic one.  The first request for a table queues
 // its compile; in blocking mode it also waits for it.
 bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t work_items, const SweepArgs& a,
-                cudaStream_t st, cudaError_t* err) {
+                cudaStream_t st, cudaError_t* err, bool loaded_only) {
 #ifdef SHK_DEBUG_BOUNDS
-    (void)e0, (void)e1, (void)block, (void)half, (void)work_items, (void)a, (void)st, (void)err;
+    (void)e0, (void)e1, (void)block, (void)half, (void)work_items, (void)a, (void)st, (void)err, (void)loaded_only;
     return false;   // the bounds-checked build checks the generic kernels
 #else
     const int mode = g_jit_mode.load();
@@ -320,7 +320,16 @@ bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t wo
         return false;
     }
     const JitEntry::Loaded* l = nullptr;
-    {
+    if (loaded_only) {
+        // only a kernel that an earlier launch on this device has loaded:
+        // no compile is queued, run or waited for, and no module is loaded
+        std::lock_guard<std::mutex> lock(g_mu);
+        auto it = g_cache.find(std::make_tuple(std::string(e0), U[0], U[1], U[2]));
+        if (it == g_cache.end() || it->second->state != JitEntry::kCompiled) return false;
+        auto d = it->second->dev.find(dev);
+        if (d == it->second->dev.end() || !d->second.ok) return false;
+        l = &d->second;
+    } else {
         std::unique_lock<std::mutex> lock(g_mu);
         JitEntry* en = find_or_queue(e0, e1, block, U, mode == 2);
         if (en == nullptr) return false;

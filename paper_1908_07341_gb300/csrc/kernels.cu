@@ -366,7 +366,8 @@ bool set_sweep_variant(int layout, int v) {
 
 cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* dst,
                             const DrawParams& P, uint32_t hs, long long* obs_cur,
-                            long long* obs_prev, long long* zero_slot, cudaStream_t st) {
+                            long long* obs_prev, long long* zero_slot, cudaStream_t st,
+                            bool loaded_only) {
     SweepArgs a = sweep_args(g, src, dst, P, hs, obs_cur, half == 0 ? obs_prev : nullptr, zero_slot);
     if (g.layout == kBitpack || g.aligned) {
         const SweepVariant* table = g.layout == kBitpack ? kBpVariants : kI8Variants;
@@ -381,7 +382,7 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
         if (rb > 1 && rb < 32 && g.nblocks / (uint32_t)rb < (uint32_t)(sm_count() * 768)) vi = fallback;
         const SweepVariant& v = table[vi];
         cudaError_t e = cudaSuccess;
-        if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e)) return e;
+        if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e, loaded_only)) return e;
         SweepKernel k = v.k[half];
         return launch_pdl(k, grid_for(k, v.block, g.nblocks), v.block, st, a);
     } else {

@@ -14,8 +14,12 @@
 // part needs no clearing: half-step A overwrites all of it before anything
 // reads it.  Two calls whose work overlaps on the GPU (on different streams,
 // or from different host threads) race on the array and give wrong results.
-#include <mutex>
-
+//
+// The call compiles and loads nothing either: a half-step runs the sweep
+// specialised for its threshold table only when an earlier call of the
+// library has already loaded that kernel on this device (loading a module
+// allocates device memory), and the generic sweep otherwise.  Both compute
+// the same spins and sums.
 #include "shaken.h"
 #include "internal.h"
 
@@ -27,10 +31,6 @@ constexpr size_t kTauBytes = SHK_STATIC_SCRATCH_PLANE_BYTES;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kRingBytes + kTauBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
 int fail(int code, const char* msg) {
     shk::set_thread_error(msg);
     return code;
@@ -38,20 +38,13 @@ int fail(int code, const char* msg) {
 
 // Device address of the scratch array on the current device.  The host-side
 // symbol is only a stand-in, so the address comes from cudaGetSymbolAddress,
-// queried once per device with that device current.
+// with the device current.  It is looked up on every call (cheap next to the
+// launches), so an address never outlives the context it belongs to.
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -69,6 +62,9 @@ extern "C" int shk_shaken_run_static(int layout, void* sigma, int L, double q, d
                     "shk_shaken_run_static: lattice too large for the static scratch "
                     "(at most 8 MiB per plane: bit-packed L <= 8192, int8 L <= 2896)");
     if (sigma == nullptr) return fail(SHK_EINVAL, "shk_shaken_run_static: sigma is NULL");
+    if (!aligned16(sigma) || (last_obs != nullptr && !aligned8(last_obs)))
+        return fail(SHK_EINVAL,
+                    "shk_shaken_run_static: sigma must be 16-byte aligned and last_obs 8-byte aligned");
     if (t0 > SHK_MAX_STEP || n_steps > SHK_MAX_STEP - t0)
         return fail(SHK_EINVAL, "shk_shaken_run_static: step index would exceed 2^31");
     uint32_t T[6];
@@ -90,10 +86,11 @@ extern "C" int shk_shaken_run_static(int layout, void* sigma, int L, double q, d
     e = cudaMemsetAsync(slot(t0), 0, kNumObs * sizeof(long long), st);
     for (uint64_t t = t0; e == cudaSuccess && t <= t_last; ++t) {
         e = launch_halfstep(g, 0, sigma, tau, P, (uint32_t)(2 * t), slot(t),
-                            t > t0 ? slot(t - 1) : nullptr, t < t_last ? slot(t + 1) : nullptr, st);
+                            t > t0 ? slot(t - 1) : nullptr, t < t_last ? slot(t + 1) : nullptr, st,
+                            /*loaded_only=*/true);
         if (e == cudaSuccess)
             e = launch_halfstep(g, 1, tau, sigma, P, (uint32_t)(2 * t + 1), slot(t), nullptr,
-                                nullptr, st);
+                                nullptr, st, /*loaded_only=*/true);
     }
     if (e == cudaSuccess) e = launch_cnn(g, sigma, slot(t_last), st);
     if (e == cudaSuccess && last_obs != nullptr)

@@ -37,16 +37,23 @@ def main() -> int:
         assert np.array_equal(lat.read_spins(0).reshape(-1), s), (L, layout)
         lat.close()
         checked.append(f"run {layout} L={L}")
-    # the one-launch (cooperative) path
-    so.shk_set_one_launch(1)
-    lat = shk.Lattice(512, "bitpack").set_seed(5, 1).set_params(0.8, 0.4).init("random", init_seed=3)
-    obs = lat.run(3, obs=True).cpu().numpy()
-    s = orc.init_plane(512, orc.INIT_RANDOM, 3, 1, 0)
-    t = orc.init_plane(512, orc.INIT_RANDOM, 3, 1, 1)
-    assert np.array_equal(obs, orc.run(s, t, 512, 0.8, 0.4, 5, 1, 0, 3))
-    lat.close()
-    so.shk_set_one_launch(0)
-    checked.append("one-launch run")
+    # the allocation-free entry point: tau plane and sums in the library's
+    # static scratch array, compared with a handle run over the same steps
+    for L, layout in ((96, "bitpack"), (257, "int8")):
+        lat = shk.Lattice(L, layout).set_seed(5, 2).set_params(0.7, 0.45).init("random", init_seed=8)
+        from tests.gpu_util import from_device_plane, to_device_plane
+        plane = to_device_plane(lat.read_spins(0).reshape(-1).copy(), L, layout)
+        last = torch.zeros(shk.NOBS, dtype=torch.int64, device="cuda")
+        want = lat.run(3, obs=True)[-1].cpu().numpy()
+        rc = so.shk_shaken_run_static(_lib.BITPACK if layout == "bitpack" else _lib.INT8, plane.data_ptr(), L,
+                                      0.7, 0.45, 5, 2, 0, 3, last.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream)
+        assert rc == _lib.OK
+        torch.cuda.synchronize()
+        assert np.array_equal(from_device_plane(plane, L, layout), lat.read_spins(0).reshape(-1)), (L, layout)
+        assert np.array_equal(last.cpu().numpy(), want), (L, layout)
+        lat.close()
+    checked.append("allocation-free run")
     # every launch shape of the sweeps at a strip-walk size
     from paper_1908_07341_gb300 import tune
     for layout in ("bitpack", "int8"):

@@ -103,6 +103,21 @@ def test_misaligned_planes_are_rejected_without_a_gpu(so):
     assert so.shk_checkerboard_run(ctypes.c_void_p(256 + 12), 64, 0.4, 1, 0, 0, 1, None, None) == _lib.EINVAL
 
 
+def test_allocation_free_run_rejects_misaligned_pointers_without_a_gpu(so):
+    # The allocation-free entry point runs the same vector-load sweeps: a sigma
+    # plane off a 16-byte boundary (or a result buffer off an 8-byte one) is
+    # refused before any CUDA call.  The pointers below are never dereferenced.
+    for layout, L in ((_lib.BITPACK, 96), (_lib.BITPACK, 4096), (_lib.INT8, 257)):
+        for off in (1, 4, 8, 12):
+            rc = so.shk_shaken_run_static(layout, 0x10000 + off, L, 0.5, 0.5, 1, 0, 0, 3, None, None)
+            assert rc == _lib.EINVAL, (layout, L, off)
+            assert b"16-byte aligned" in so.shk_last_error(None)
+        rc = so.shk_shaken_run_static(layout, 0x10000, L, 0.5, 0.5, 1, 0, 0, 3, 0x20004, None)
+        assert rc == _lib.EINVAL
+        assert b"8-byte aligned" in so.shk_last_error(None)
+    assert so.shk_shaken_run_static(_lib.BITPACK, None, 96, 0.5, 0.5, 1, 0, 0, 3, None, None) == _lib.EINVAL
+
+
 def test_handle_state_checks_without_a_gpu(so):
     # A handle over a fake (never dereferenced) aligned address: configuration
     # calls are host-only, and running before set_params is refused.
@@ -202,15 +217,6 @@ def test_coalescence_and_cftp_argument_checks_without_gpu():
                        dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL       # still k_max
     assert so.shk_cftp(0, 1, L.ctypes.data, None, J.ctypes.data, seed.ctypes.data, ids.ctypes.data, 10,
                        dummy, 128, dummy, nc, ks.ctypes.data, None) == _lib.EINVAL       # shaken needs q
-
-
-def test_barrier_timeout_test_argument_checks_without_gpu():
-    so = _lib.lib()
-    flag = np.zeros(1, dtype=np.int32)
-    assert so.shk_barrier_timeout_test(0, ctypes.c_void_p(256), flag.ctypes.data, None) == _lib.EINVAL
-    assert so.shk_barrier_timeout_test(1 << 21, ctypes.c_void_p(256), flag.ctypes.data, None) == _lib.EINVAL
-    assert so.shk_barrier_timeout_test(10, None, flag.ctypes.data, None) == _lib.EINVAL
-    assert so.shk_set_one_launch(0) == _lib.OK
 
 
 def test_step_counters_do_not_wrap():

@@ -78,3 +78,33 @@ def test_static_scratch_without_result_buffer():
     assert _run_static(layout, plane, L, 1.0, 0.3, 7, 0, 0, 5, None) == _lib.OK
     torch.cuda.synchronize()
     assert np.array_equal(from_device_plane(plane, L, layout), ref.read_spins(0).reshape(-1))
+
+
+def test_static_scratch_queues_no_compile_even_in_blocking_mode():
+    # Compiling a specialised sweep, or loading one as a module, allocates, so
+    # the allocation-free entry point must do neither, whatever the
+    # specialisation mode.  With blocking compiles requested, a call with a
+    # threshold table the process has never seen still queues no compile, and
+    # its spins equal those of a handle run with specialisation off.
+    L, layout, q, J, seed = 4096, "bitpack", 0.9137, 0.4071, 77
+    ref = shk.Lattice(L, layout).set_seed(seed, 0).set_params(q, J).init("random", init_seed=4)
+    sigma0 = ref.read_spins(0).reshape(-1).copy()
+    mode = shk.specialize()
+    try:
+        shk.specialize(shk.lattice.SPECIALIZE_OFF)
+        want = ref.run(3, obs=True)[-1].cpu().numpy()
+        want_sigma = ref.read_spins(0).reshape(-1)
+        shk.specialize(shk.lattice.SPECIALIZE_BLOCKING)
+        before = shk.specialize_status()
+        plane = to_device_plane(sigma0, L, layout)
+        last = torch.zeros(shk.NOBS, dtype=torch.int64, device="cuda")
+        assert _run_static(layout, plane, L, q, J, seed, 0, 0, 3, last) == _lib.OK
+        torch.cuda.synchronize()
+        after = shk.specialize_status()
+        assert (after["compiled"], after["queued"], after["failed"]) == \
+            (before["compiled"], before["queued"], before["failed"])
+        assert np.array_equal(from_device_plane(plane, L, layout), want_sigma)
+        assert np.array_equal(last.cpu().numpy(), want)
+    finally:
+        shk.specialize(mode)
+
