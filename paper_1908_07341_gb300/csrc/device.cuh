@@ -193,13 +193,29 @@ struct PhiloxPrefix {
     uint32_t A, K2, K3, H3, D;
 };
 
-template <class PP>
-__device__ __forceinline__ uint4 philox_call_pre(uint32_t w, const PhiloxPrefix& u, const PP& P) {
+//
+// The call index c enters round 1 only through an XOR into the third word,
+// which round 2 multiplies by a constant; so A and K2 are the same for all
+// calls of a half-step, and the two varying products of rounds 2 and 3
+// (M0 x1 and M1 x2) depend on the block only.  A block computes them once
+// (PhiloxBlock) and shares them among its calls.
+struct PhiloxBlock {
+    uint32_t h1, l1, l0;   // hi(M1 x2), lo(M1 x2), lo(M0 x1)
+};
+
+__device__ __forceinline__ PhiloxBlock philox_block(uint32_t w, const PhiloxPrefix& u) {
     const uint32_t x1 = u.A ^ w;
     const uint32_t x2 = __umulhi(kPhiloxM0, x1) ^ u.K2;
-    uint32_t c0 = __umulhi(kPhiloxM1, x2) ^ u.K3;
-    uint32_t c1 = kPhiloxM1 * x2;
-    uint32_t c2 = u.H3 ^ (kPhiloxM0 * x1);
+    return {__umulhi(kPhiloxM1, x2), kPhiloxM1 * x2, kPhiloxM0 * x1};
+}
+
+// Rounds 4 to 10 of one call from the block's shared products and the call's
+// own uniform words (K3, H3, D).
+template <class PP>
+__device__ __forceinline__ uint4 philox_call_blk(const PhiloxBlock& b, const PhiloxPrefix& u, const PP& P) {
+    uint32_t c0 = b.h1 ^ u.K3;
+    uint32_t c1 = b.l1;
+    uint32_t c2 = u.H3 ^ b.l0;
     uint32_t c3 = u.D;
 #pragma unroll
     for (int r = 3; r < 10; ++r) {
@@ -215,6 +231,11 @@ __device__ __forceinline__ uint4 philox_call_pre(uint32_t w, const PhiloxPrefix&
         c3 = lo0;
     }
     return make_uint4(c0, c1, c2, c3);
+}
+
+template <class PP>
+__device__ __forceinline__ uint4 philox_call_pre(uint32_t w, const PhiloxPrefix& u, const PP& P) {
+    return philox_call_blk(philox_block(w, u), u, P);
 }
 
 // Threshold bit masks of random plane b: all ones where bit 31-b of the
@@ -235,18 +256,33 @@ __device__ __forceinline__ uint32_t jit_plane_bit(uint32_t u, int b) {
 #define SHK_PLANE_D12(P, b) ((P).d12[b])
 #endif
 
-// Applies the four planes of call c to the state (und, up) of one block.
+// Applies the four planes of call c to the state (und, v) of one block.
+// g is the raw random bit that would decide a site as +1.  A site is decided
+// at the first plane whose random bit differs from g, and its result is then
+// that plane's g.  v takes g at every plane while the site is undecided and
+// keeps it from then on (a bitwise select); und clears at the deciding
+// plane.  Two three-input logic operations per plane.  The result of the
+// block is draw_result(und, v, F) after the last plane (v alone once und is
+// 0).
 template <class PP>
 __device__ __forceinline__ void apply_planes(const uint4& R, int c, const BlockClass& k, uint32_t& und,
-                                             uint32_t& up, const PP& P) {
+                                             uint32_t& v, const PP& P) {
     const uint32_t x[4] = {R.x, R.y, R.z, R.w};
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int b = 4 * c + m;
         const uint32_t g = k.F ^ SHK_PLANE_M0(P, b) ^ (k.Cg & SHK_PLANE_D01(P, b)) ^ (k.C2 & SHK_PLANE_D12(P, b));
-        up |= und & ~x[m] & g;
+        v = (und & g) | (~und & v);
         und &= ~(x[m] ^ g);
     }
+}
+
+// Result of a block whose undecided sites (und) tied their thresholds in all
+// 32 planes: a uniform equal to its threshold is not below it, so a + site
+// stays -1, and a - site (which compares its complemented uniform) comes out
+// +1, i.e. the tie result is F.  Decided sites take v.
+__device__ __forceinline__ uint32_t draw_result(uint32_t und, uint32_t v, uint32_t F) {
+    return (und & F) | (~und & v);
 }
 
 // Phase 1: calls 0 and 1 for one block.
@@ -263,13 +299,15 @@ __device__ __forceinline__ void draw_first_two(const BlockClass& k, uint32_t w, 
 }
 
 // Phase 1 with the host-computed round prefixes of the half-step (pre[c] for
-// call c); the same draw as draw_first_two.
+// call c); the same draw as draw_first_two.  The two calls share the block's
+// products of rounds 2 and 3.
 template <class PP>
 __device__ __forceinline__ void draw_first_two_pre(const BlockClass& k, uint32_t w, uint32_t valid,
                                                    const PhiloxPrefix (&pre)[8], const PP& P, uint32_t& und,
                                                    uint32_t& up) {
-    const uint4 R0 = philox_call_pre(w, pre[0], P);
-    const uint4 R1 = philox_call_pre(w, pre[1], P);
+    const PhiloxBlock pb = philox_block(w, pre[0]);
+    const uint4 R0 = philox_call_blk(pb, pre[0], P);
+    const uint4 R1 = philox_call_blk(pb, pre[1], P);
     und = valid;
     up = 0;
     apply_planes(R0, 0, k, und, up, P);
@@ -280,13 +318,14 @@ __device__ __forceinline__ void draw_first_two_pre(const BlockClass& k, uint32_t
 template <class PP>
 __device__ __forceinline__ uint32_t draw_rest_pre(const BlockClass& k, uint32_t w, uint32_t und, uint32_t up,
                                                   const PhiloxPrefix (&pre)[8], const PP& P) {
+    const PhiloxBlock pb = philox_block(w, pre[0]);
 #pragma unroll
     for (int c = 2; c < 8; ++c) {
         if (!__any_sync(0xffffffffu, und != 0u)) break;
-        const uint4 R = philox_call_pre(w, pre[c], P);
+        const uint4 R = philox_call_blk(pb, pre[c], P);
         apply_planes(R, c, k, und, up, P);
     }
-    return up | (und & k.F);
+    return draw_result(und, up, k.F);
 }
 
 // Phase 2: calls 2..7 with the lazy exit; all 32 lanes call it together.
@@ -299,7 +338,7 @@ __device__ __forceinline__ uint32_t draw_rest(const BlockClass& k, uint32_t w, u
         const uint4 R = philox_call(w, hs, c, P);
         apply_planes(R, c, k, und, up, P);
     }
-    return up | (und & k.F);
+    return draw_result(und, up, k.F);
 }
 
 // One block with precomputed class masks (lazy loop to the end; all lanes of
@@ -314,7 +353,7 @@ __device__ __forceinline__ uint32_t draw_block_class(const BlockClass& k, uint32
         apply_planes(R, c, k, und, up, P);
         if (c < 7 && !__any_sync(0xffffffffu, und != 0u)) break;
     }
-    return up | (und & k.F);
+    return draw_result(und, up, k.F);
 }
 
 // One block (the common case).

@@ -107,7 +107,7 @@ void set_thread_error(const char* msg);
 // (default), 2 compile at first use and wait for it.
 struct SweepArgs;
 bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t work_items, const SweepArgs& a,
-                cudaStream_t st, cudaError_t* err, bool loaded_only = false);
+                cudaStream_t st, cudaError_t* err, bool loaded_only = false, int waves = 1);
 extern std::atomic<int> g_jit_mode;
 // Queues (wait: and waits for) the specialised compile of sweep variant
 // `variant` of `layout` for threshold table T; SHK_OK or an error status with

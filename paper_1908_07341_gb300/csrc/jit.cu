@@ -305,9 +305,10 @@ static void thresholds_of(const DrawParams& P, uint32_t U[3]) {
 // the caller launches the generic one.  The first request for a table queues
 // its compile; in blocking mode it also waits for it.
 bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t work_items, const SweepArgs& a,
-                cudaStream_t st, cudaError_t* err, bool loaded_only) {
+                cudaStream_t st, cudaError_t* err, bool loaded_only, int waves) {
 #ifdef SHK_DEBUG_BOUNDS
-    (void)e0, (void)e1, (void)block, (void)half, (void)work_items, (void)a, (void)st, (void)err, (void)loaded_only;
+    (void)e0, (void)e1, (void)block, (void)half, (void)work_items, (void)a, (void)st, (void)err, (void)loaded_only,
+        (void)waves;
     return false;   // the bounds-checked build checks the generic kernels
 #else
     const int mode = g_jit_mode.load();
@@ -349,7 +350,7 @@ bool jit_launch(const char* e0, const char* e1, int block, int half, uint32_t wo
         l = loaded_on(en, dev);
         if (l == nullptr) return false;
     }
-    const uint64_t full = (uint64_t)l->per_sm[half] * sm_count();
+    const uint64_t full = (uint64_t)l->per_sm[half] * sm_count() * (uint64_t)(waves > 0 ? waves : 1);
     const uint64_t need = ((uint64_t)work_items + block - 1) / block;
     const int grid = (int)std::max<uint64_t>(1, std::min(full, need));
     void* args[] = {const_cast<SweepArgs*>(&a)};

@@ -292,6 +292,7 @@ struct SweepVariant {
     int row_blocks;     // rows must hold a multiple of this many blocks (32: L % 1024 == 0)
     const char* name;
     const char* jit[2]; // the same kernels as name expressions for run-time compilation (jit.cu), or null
+    int waves;          // grid: at most this many full waves of resident blocks
 };
 
 #define SHK_JIT_NAMES(kernel, args) {"shk::" #kernel "<0, " args ">", "shk::" #kernel "<1, " args ">"}
@@ -301,6 +302,10 @@ struct SweepVariant {
 static const SweepVariant kBpVariants[] = {
     {{k_sweep_qv<0, 4, 256, 3>, k_sweep_qv<1, 4, 256, 3>}, 256, 4, "queue-v4-256x3",
      SHK_JIT_NAMES(k_sweep_qv, "4, 256, 3")},
+    {{k_sweep_qv<0, 4, 256, 3>, k_sweep_qv<1, 4, 256, 3>}, 256, 4, "queue-v4-256x3-w2",
+     SHK_JIT_NAMES(k_sweep_qv, "4, 256, 3"), 2},
+    {{k_sweep_qv<0, 4, 256, 3>, k_sweep_qv<1, 4, 256, 3>}, 256, 4, "queue-v4-256x3-w4",
+     SHK_JIT_NAMES(k_sweep_qv, "4, 256, 3"), 4},
     {{k_sweep_q<0, kBitpack, 256, 3>, k_sweep_q<1, kBitpack, 256, 3>}, 256, 1, "queue-256x3",
      SHK_JIT_NAMES(k_sweep_q, "1, 256, 3")},
     {{k_sweep_qv<0, 2, 256, 3>, k_sweep_qv<1, 2, 256, 3>}, 256, 2, "queue-v2-256x3",
@@ -319,6 +324,8 @@ static const SweepVariant kBpVariants[] = {
 static const SweepVariant kI8Variants[] = {
     {{k_sweep_strip_async<0, kInt8, 256, 3, 2>, k_sweep_strip_async<1, kInt8, 256, 3, 2>}, 256, 32,
      "strip-async2-256x3", SHK_JIT_NAMES(k_sweep_strip_async, "2, 256, 3, 2")},
+    {{k_sweep_strip_async<0, kInt8, 256, 3, 2>, k_sweep_strip_async<1, kInt8, 256, 3, 2>}, 256, 32,
+     "strip-async2-256x3-w2", SHK_JIT_NAMES(k_sweep_strip_async, "2, 256, 3, 2"), 2},
     {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, 32, "strip-256x3",
      SHK_JIT_NAMES(k_sweep_strip, "2, 256, 3")},
     {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, 1, "queue-256x3",
@@ -330,8 +337,8 @@ static const SweepVariant kI8Variants[] = {
 
 constexpr int kNumBpVariants = sizeof(kBpVariants) / sizeof(kBpVariants[0]);
 constexpr int kNumI8Variants = sizeof(kI8Variants) / sizeof(kI8Variants[0]);
-constexpr int kBpRowFallback = 1;   // variant used when rows are too short for the chosen one (queue-256x3)
-constexpr int kI8RowFallback = 2;
+constexpr int kBpRowFallback = 3;   // variant used when rows are too short for the chosen one (queue-256x3)
+constexpr int kI8RowFallback = 3;
 
 static std::atomic<int> g_bp_variant{0};
 static std::atomic<int> g_i8_variant{0};
@@ -382,9 +389,10 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
         if (rb > 1 && rb < 32 && g.nblocks / (uint32_t)rb < (uint32_t)(sm_count() * 768)) vi = fallback;
         const SweepVariant& v = table[vi];
         cudaError_t e = cudaSuccess;
-        if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e, loaded_only)) return e;
+        const int waves = v.waves > 0 ? v.waves : 1;
+        if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e, loaded_only, waves)) return e;
         SweepKernel k = v.k[half];
-        return launch_pdl(k, grid_for(k, v.block, g.nblocks), v.block, st, a);
+        return launch_pdl(k, grid_for(k, v.block, g.nblocks, waves), v.block, st, a);
     } else {
         const int block = 256;
         SweepKernel k = half == 0 ? k_sweep_i8g<0> : k_sweep_i8g<1>;

@@ -169,8 +169,8 @@ __device__ __forceinline__ void draw_coupled(const BlockClass (&k)[2], uint32_t 
         apply_planes(R, c, k[1], und[1], up[1], P);
         if (c < 7 && !__any_sync(0xffffffffu, (und[0] | und[1]) != 0u)) break;
     }
-    up[0] |= und[0] & k[0].F;
-    up[1] |= und[1] & k[1].F;
+    up[0] = draw_result(und[0], up[0], k[0].F);
+    up[1] = draw_result(und[1], up[1], k[1].F);
 }
 
 // One full step with index t of both chains, driven by the same uniforms

@@ -169,12 +169,16 @@ inline cudaError_t launch_pdl(K kernel, int grid, int block, cudaStream_t st, co
     return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-// Grid of at most one full wave of resident blocks (the kernels stride over
-// their work), never more blocks than work items need.
+// Grid of at most `waves` full waves of resident blocks (the kernels stride
+// over their work), never more blocks than work items need.  With more than
+// one wave the blocks of the later waves start as earlier ones retire, which
+// evens out the end of the launch; programmatic dependent launch stays safe,
+// because the next kernel launches only once every block of this one has
+// started.
 template <class K>
-inline int grid_for(K kernel, int block, uint64_t work_items) {
+inline int grid_for(K kernel, int block, uint64_t work_items, int waves = 1) {
     const int per_sm = blocks_per_sm(reinterpret_cast<const void*>(kernel), block);
-    const uint64_t full = (uint64_t)per_sm * sm_count();
+    const uint64_t full = (uint64_t)per_sm * sm_count() * (uint64_t)waves;
     const uint64_t need = (work_items + block - 1) / block;
     return (int)std::max<uint64_t>(1, std::min(full, need));
 }

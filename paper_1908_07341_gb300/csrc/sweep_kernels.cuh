@@ -15,29 +15,37 @@ namespace shk {
 
 // ------------------------------------------------------------ half-step sweeps
 
+// Per-thread sums of a half-step, kept as raw counts and turned into the
+// signed sums once per thread (finish_step): acc[0] = up sites drawn,
+// acc[1] and acc[2] = disagreeing pairs (A: sigma with its down and left
+// neighbours, for C_nn; B: sigma with tau, for S_q, and sigma with tau's up
+// and right neighbours, for S_J), acc[3] = sites drawn.  With a full valid
+// mask the masking and the site count fold to constants.
 template <int HALF>
-__device__ __forceinline__ void accumulate_step(int (&acc)[3], uint32_t up, uint32_t S, uint32_t N1,
+__device__ __forceinline__ void accumulate_step(int (&acc)[4], uint32_t up, uint32_t S, uint32_t N1,
                                                 uint32_t N2, uint32_t valid, bool cnn) {
-    const int nv = __popc(valid);
+    acc[3] += __popc(valid);
+    acc[0] += __popc(up);
     if (HALF == 0) {
-        acc[0] += 2 * __popc(up) - nv;                                              // M_tau
-        if (cnn) acc[1] += 2 * nv - 2 * (__popc((S ^ N1) & valid) + __popc((S ^ N2) & valid));
+        if (cnn) acc[1] += __popc((S ^ N1) & valid) + __popc((S ^ N2) & valid);
     } else {
-        acc[0] += 2 * __popc(up) - nv;                                              // M_sigma
-        acc[1] += nv - 2 * __popc((up ^ S) & valid);                                // S_q
-        acc[2] += 2 * nv - 2 * (__popc((up ^ N1) & valid) + __popc((up ^ N2) & valid));  // S_J
+        acc[1] += __popc((up ^ S) & valid);
+        acc[2] += __popc((up ^ N1) & valid) + __popc((up ^ N2) & valid);
     }
 }
 
+// A: M_tau = 2 up - n, C_nn = 2 n - 2 disagreeing; B: M_sigma, S_q = n - 2
+// disagreeing, S_J = 2 n - 2 disagreeing.  Each is added to the step's row.
 template <int HALF>
-__device__ __forceinline__ void finish_step(const int (&acc)[3], const SweepArgs& a) {
+__device__ __forceinline__ void finish_step(const int (&acc)[4], const SweepArgs& a) {
+    const int n = acc[3];
     if (HALF == 0) {
-        const int v[2] = {acc[0], acc[1]};
+        const int v[2] = {2 * acc[0] - n, 2 * n - 2 * acc[1]};
         long long* const d[2] = {a.obs_cur ? a.obs_cur + 1 : nullptr,
                                  a.obs_prev ? a.obs_prev + 4 : nullptr};
         block_accumulate<2>(v, d);
     } else {
-        const int v[3] = {acc[0], acc[1], acc[2]};
+        const int v[3] = {2 * acc[0] - n, n - 2 * acc[1], 2 * n - 2 * acc[2]};
         long long* const d[3] = {a.obs_cur ? a.obs_cur + 0 : nullptr,
                                  a.obs_cur ? a.obs_cur + 2 : nullptr,
                                  a.obs_cur ? a.obs_cur + 3 : nullptr};
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_bp(const SweepArgs a) {
     const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32 * ILP;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     // nblocks is a multiple of 32, so a 32-block group is all in or all out and
     // the validity tests below are uniform across the warp.
     uint32_t base = gwarp * 32 * ILP;
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_i8a(const SweepArgs a) {
     const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     uint32_t base = gwarp * 32;
     RawI8 raw;
     if (PREFETCH && base < a.nblocks) raw = load_i8<HALF>(src, base + lane, a);
@@ -206,7 +214,7 @@ constexpr int kQueueFields = 6;
 
 template <int HALF, int LAYOUT>
 __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uint32_t up, uint32_t S,
-                                             uint32_t N1, uint32_t N2, bool cnn, int (&acc)[3]) {
+                                             uint32_t N1, uint32_t N2, bool cnn, int (&acc)[4]) {
     if (LAYOUT == kBitpack) {
         *checked(static_cast<uint32_t*>(a.dst), w, a.nblocks, SHK_SITE) = up;
     } else {
@@ -222,7 +230,7 @@ __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uin
 // Continues the `count` (<= 32) oldest parked blocks; all lanes call it.
 template <int HALF, int LAYOUT, class PP>
 __device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, uint32_t (*q)[kQueueCap],
-                                            uint32_t head, int count, bool cnn, int (&acc)[3]) {
+                                            uint32_t head, int count, bool cnn, int (&acc)[4]) {
     const uint32_t lane = threadIdx.x & 31;
     const bool has = (int)lane < count;
     const uint32_t i = (head + lane) & (kQueueCap - 1);
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     uint32_t head = 0;
     int count = 0;
     const uint32_t below = (1u << lane) - 1u;
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_qv(const SweepArgs a) {
     uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     uint32_t head = 0;
     int count = 0;
     const uint32_t below = (1u << lane) - 1u;
@@ -464,7 +472,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
     const DrawParams& P = a.P;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     uint32_t head = 0;
     int count = 0;
     const uint32_t below = (1u << lane) - 1u;
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
     uint32_t (*q)[kQueueCap] = qbuf[wib];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     uint32_t head = 0;
     int count = 0;
     const uint32_t below = (1u << lane) - 1u;
@@ -702,7 +710,7 @@ __global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
-    int acc[3] = {0, 0, 0};
+    int acc[4] = {0, 0, 0, 0};
     for (uint32_t base = gwarp * 32; base < a.nblocks; base += nwarps * 32) {
         const uint32_t w = base + lane;
         const bool active = w < a.nblocks;
