@@ -464,6 +464,16 @@ int shk_server_cancel(shk_server* s, uint64_t job_id);
 int shk_server_tick(shk_server* s, int* n_active, int* n_pending);
 int shk_server_poll(shk_server* s, shk_result* out, int max, int* n_out);
 int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes);
+/* Spins of a job that is running (admitted, not yet retired), between ticks:
+ * plane 0 = sigma, 1 = tau as int8 +/-1 into host_out (L*L bytes, row-major;
+ * bytes is the buffer's size), and in *steps_done the full steps it has
+ * completed (the state is the one after that step, Eqs. leftTrans /
+ * rightTrans).  No counterpart in the paper; it lets a caller inspect or
+ * check a job in flight.  Synchronises the server's stream.  Errors:
+ * SHK_EINVAL for a NULL argument, a bad plane, or a job id that is not
+ * running; SHK_ENOMEM if bytes < L*L (nothing written). */
+int shk_server_read_job(shk_server* s, uint64_t job_id, int plane, int8_t* host_out, size_t bytes,
+                        uint64_t* steps_done);
 
 /* ------------------------------------------------------------ allocation-free run */
 

@@ -95,6 +95,7 @@ SIGNATURES = {
     "shk_server_tick": (_i, [_vp, _vp, _vp]),
     "shk_server_poll": (_i, [_vp, _vp, _i, _vp]),
     "shk_server_stats": (_i, [_vp, _vp, _vp]),
+    "shk_server_read_job": (_i, [_vp, _u64, _i, _vp, _sz, _vp]),
     "shk_shaken_run_static": (_i, [_i, _vp, _i, _d, _d, _u64, _u32, _u64, _u64, _vp, _vp]),
 }
 

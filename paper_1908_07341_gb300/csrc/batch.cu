@@ -1182,6 +1182,30 @@ int shk_server_poll(shk_server* s, shk_result* out, int max, int* n_out) {
     return SHK_OK;
 }
 
+int shk_server_read_job(shk_server* s, uint64_t job_id, int plane, int8_t* host_out, size_t bytes,
+                        uint64_t* steps_done) {
+    if (!s || !host_out || !steps_done || (plane != 0 && plane != 1))
+        return sfail(s, SHK_EINVAL, "shk_server_read_job: bad argument");
+    for (int i = 0; i < s->max_slots; ++i) {
+        const Slot& sl = s->slots[i];
+        if (!sl.used || sl.job_id != job_id) continue;
+        const BatchLattice& B = s->lat[i];
+        const size_t off = plane == 0 ? B.sigma_off[B.parity] : B.tau_off;
+        const int64_t N = (int64_t)B.L * B.L;
+        if (bytes < (size_t)N)
+            return sfail(s, SHK_ENOMEM, "shk_server_read_job: %zu bytes given, %lld needed", bytes, (long long)N);
+        std::vector<uint32_t> words((size_t)(N / 32));
+        cudaError_t e = cudaMemcpyAsync(words.data(), s->dev + off, words.size() * 4, cudaMemcpyDeviceToHost,
+                                        s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return sfail(s, SHK_ECUDA, "shk_server_read_job: %s", cudaGetErrorString(e));
+        for (int64_t u = 0; u < N; ++u) host_out[u] = ((words[u >> 5] >> (u & 31)) & 1u) ? 1 : -1;
+        *steps_done = sl.job.n_steps - sl.remaining;
+        return SHK_OK;
+    }
+    return sfail(s, SHK_EINVAL, "shk_server_read_job: job %llu is not running", (unsigned long long)job_id);
+}
+
 int shk_server_stats(shk_server* s, uint64_t* tick, size_t* used_bytes) {
     if (!s) return sfail(nullptr, SHK_EINVAL, "shk_server_stats: NULL handle");
     if (tick) *tick = s->tick;

@@ -119,6 +119,15 @@ class Server:
                                         for k, v in r.items()}) + "\n")
         return out
 
+    def read_job(self, job_id: int, L: int, plane: int = 0) -> tuple[np.ndarray, int]:
+        """Spins (int8 +/-1, L x L) of a running job of side L between ticks,
+        and the full steps it has completed."""
+        out = np.zeros(int(L) * int(L), dtype=np.int8)
+        steps = ctypes.c_uint64()
+        _check(lib().shk_server_read_job(self._h, int(job_id), int(plane), out.ctypes.data, out.size,
+                                         ctypes.byref(steps)), self._h)
+        return out.reshape(int(L), int(L)), int(steps.value)
+
     def stats(self):
         t, u = ctypes.c_uint64(), ctypes.c_size_t()
         _check(lib().shk_server_stats(self._h, ctypes.byref(t), ctypes.byref(u)), self._h)

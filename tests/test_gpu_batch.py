@@ -3,6 +3,9 @@ lattice runs: every lattice of a batch must follow exactly the trajectory
 shk_run gives it, and the batch statistics must equal the sums of the single
 runs' per-step observables (all integers, compared exactly).  The single-
 lattice path is itself checked against the oracle in test_gpu_parity."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -124,3 +127,67 @@ def test_full_phase_diagram_batch_spot_checks(orc):
                 96, 8, want_obs=False)
         assert np.array_equal(b.read_spins(i, 0).reshape(-1), sigma), i
         assert np.array_equal(b.read_spins(i, 1).reshape(-1), tau), i
+
+
+def test_phase_diagram_batch_against_the_oracle(orc):
+    """The batched configuration at its full size and in the benchmark's tuned
+    launch shape (2 steps per launch, 256 threads, 2^17-site tiles): all 1024
+    lattices of the phase diagram (L log-uniform in {32, ..., 2048}, one
+    (q, J) cell each) run 56 steps with a 16-step burn-in.
+    - Every lattice with L <= 256 is recomputed by the oracle from its random
+      start: final sigma and tau, the five sums of the last step, and the
+      eleven exact statistics of the 40 measured steps (Eq. fact applied to
+      each lattice on its own, as in the task-parallel runs of the paper).
+    - 48 larger lattices (16 each of L = 512, 1024, 2048, whose tiles carry
+      recomputed halo rows) are spot-checked over one launch: the oracle takes
+      the GPU's sigma after step 56 and runs steps 56 and 57; sigma, tau and
+      the last step's sums must agree after the GPU's next launch.
+    The oracle runs on every host core (its C calls release the interpreter
+    lock); it shares no code with the GPU path."""
+    w = workloads.phase_diagram_batch()
+    n, burn, k = 56, 16, 2
+    b = Batch(w["L"], w["q"], w["J"], w["seed"], w["lattice_id"]).configure(k, 256, 1 << 17)
+    b.init("random", init_seed=w["init_seed"])
+    b.run(n, burn_in=burn)
+    stats, last = b.read_stats(), b.read_observables()
+    small = [i for i in range(len(w["L"])) if w["L"][i] <= 256]
+    assert len(small) > 500
+
+    def cfg(i):
+        return (int(w["L"][i]), float(w["q"][i]), float(w["J"][i]), int(w["seed"][i]), int(w["lattice_id"][i]))
+
+    def full(i):
+        L, q, J, seed, lid = cfg(i)
+        s = orc.init_plane(L, orc.INIT_RANDOM, w["init_seed"], lid, 0)
+        t = orc.init_plane(L, orc.INIT_RANDOM, w["init_seed"], lid, 1)
+        return i, s, t, orc.run(s, t, L, q, J, seed, lid, 0, n)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for i, s, t, obs in ex.map(full, small):
+            assert np.array_equal(b.read_spins(i, 0).reshape(-1), s), i
+            assert np.array_equal(b.read_spins(i, 1).reshape(-1), t), i
+            assert np.array_equal(last[i], obs[-1]), i
+            assert np.array_equal(stats[i], stats_from_observables(obs[burn:])), i
+
+    rng = np.random.default_rng(56)
+    large = []
+    for L in (512, 1024, 2048):
+        idx = np.flatnonzero(w["L"] == L)
+        large += rng.choice(idx, size=min(16, idx.size), replace=False).tolist()
+    assert len(large) >= 32
+    before = {i: b.read_spins(i, 0).reshape(-1).copy() for i in large}
+    b.run(k)
+    last = b.read_observables()
+
+    def spot(i):
+        L, q, J, seed, lid = cfg(i)
+        s = before[i].copy()
+        t = np.zeros(L * L, np.int8)
+        return i, s, t, orc.run(s, t, L, q, J, seed, lid, n, k)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for i, s, t, obs in ex.map(spot, large):
+            assert np.array_equal(b.read_spins(i, 0).reshape(-1), s), i
+            assert np.array_equal(b.read_spins(i, 1).reshape(-1), t), i
+            assert np.array_equal(last[i], obs[-1]), i
+

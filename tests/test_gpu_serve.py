@@ -1,6 +1,9 @@
 """Serving with continuous batching: jobs admitted at different ticks share
 launches, yet each job's result (exact statistics, last observables, hash of
 the final sigma) is the same alone, in the mix, and as a single-lattice run."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import pytest
 import torch
@@ -196,3 +199,99 @@ def test_serving_stream_jobs_spot_checked_against_the_oracle(orc):
         assert np.array_equal(got[i]["stats"], stats_from_observables(obs[j["burn_in"]:])), i
         assert np.array_equal(got[i]["last_obs"], obs[-1]), i
         assert got[i]["sigma_hash"] == fnv1a64(pack_bits(s).view(np.uint8).tobytes()), i
+
+
+def test_serving_stream_mixed_jobs_against_the_oracle(orc):
+    """40 jobs of the serving workload (the first 400 jobs of the Poisson
+    stream: L log-uniform in [64, 4096], q, J uniform, steps log-uniform in
+    [10^3, 10^5], seed 5, lattice id = job index) in one mix, in the
+    benchmark's launch shape (2 steps per launch, 16 launches per tick, 256
+    threads, 2^18-site tiles):
+    - 32 jobs spread over the whole range of L (the largest included) are
+      spot-checked in flight after a tick of that shape: the test reads each
+      job's sigma and step count between ticks (shk_server_read_job), the
+      server runs one tick of a single launch (2 steps, every job in the mix
+      advancing), sigma and tau are read again, and the oracle runs the same
+      two steps from the GPU's sigma; the checked jobs are then cancelled;
+    - the 8 cheapest jobs run to completion and are recomputed by the oracle
+      from their random starts: the exact statistics after burn-in, the last
+      step's sums and the hash of the final sigma."""
+    from paper_1908_07341_gb300 import workloads
+    from paper_1908_07341_gb300.lattice import pack_bits
+    w = workloads.serving_stream(n_jobs=400)
+    jobs = w["jobs"]
+    cost = np.array([j["L"] ** 2 * j["n_steps"] for j in jobs], dtype=np.float64)
+    full = np.argsort(cost)[:8].tolist()
+    rest = sorted((i for i in range(len(jobs)) if i not in full), key=lambda i: (jobs[i]["L"], i))
+    spot = sorted({rest[int(round(x))] for x in np.linspace(0, len(rest) - 1, 32)})
+    assert len(spot) == 32 and max(jobs[i]["L"] for i in spot) == max(j["L"] for j in jobs)
+    assert all(jobs[i]["n_steps"] > 34 for i in spot)
+    srv = Server(max_slots=64, arena_bytes=1 << 30).configure(steps_per_launch=2, launches_per_tick=16,
+                                                              block_threads=256, tile_sites=1 << 18)
+    ids = {srv.submit(**jobs[i]): i for i in sorted(set(full) | set(spot))}
+    job_id = {i: jid for jid, i in ids.items()}
+    got = {}
+    srv.tick()                                      # admits all 40; 32 steps of every job
+    got.update({ids[r["job_id"]]: r for r in srv.poll()})
+    before = {i: srv.read_job(job_id[i], jobs[i]["L"], 0) for i in spot}
+    srv.configure(steps_per_launch=2, launches_per_tick=1, block_threads=256, tile_sites=1 << 18)
+    srv.tick()
+    got.update({ids[r["job_id"]]: r for r in srv.poll()})
+    after = {i: (srv.read_job(job_id[i], jobs[i]["L"], 0), srv.read_job(job_id[i], jobs[i]["L"], 1)[0])
+             for i in spot}
+    srv.configure(steps_per_launch=2, launches_per_tick=16, block_threads=256, tile_sites=1 << 18)
+    for i in spot:
+        srv.cancel(job_id[i])
+
+    def spot_check(i):
+        j = jobs[i]
+        (s0, t0) = before[i]
+        s = s0.reshape(-1).copy()
+        t = np.zeros_like(s)
+        obs = orc.run(s, t, j["L"], j["q"], j["J"], j["seed"], j["lattice_id"], t0, 2)
+        return i, t0, s, t, obs
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for i, t0, s, t, obs in ex.map(spot_check, spot):
+            (s1, t1), tau1 = after[i]
+            assert t0 == 32 and t1 == 34, (i, t0, t1)
+            assert np.array_equal(s1.reshape(-1), s), i
+            assert np.array_equal(tau1.reshape(-1), t), i
+    for _ in range(100_000):
+        if all(i in got and got[i]["status"] == 0 for i in full):
+            break
+        srv.tick()
+        got.update({ids[r["job_id"]]: r for r in srv.poll()})
+    for i in spot:
+        assert got[i]["status"] == -7, i          # SHK_ECANCELLED
+    for i in full:
+        j = jobs[i]
+        L = j["L"]
+        s = orc.init_plane(L, orc.INIT_RANDOM, j["init_seed"], j["lattice_id"], 0)
+        t = orc.init_plane(L, orc.INIT_RANDOM, j["init_seed"], j["lattice_id"], 1)
+        obs = orc.run(s, t, L, j["q"], j["J"], j["seed"], j["lattice_id"], 0, j["n_steps"])
+        assert got[i]["status"] == 0 and got[i]["steps_done"] == j["n_steps"]
+        assert np.array_equal(got[i]["stats"], stats_from_observables(obs[j["burn_in"]:])), i
+        assert np.array_equal(got[i]["last_obs"], obs[-1]), i
+        assert got[i]["sigma_hash"] == fnv1a64(pack_bits(s).view(np.uint8).tobytes()), i
+    srv.close()
+
+
+def test_read_job_refuses_unknown_jobs_and_short_buffers():
+    srv = Server(max_slots=2, arena_bytes=8 << 20).configure(steps_per_launch=2, launches_per_tick=1)
+    jid = srv.submit(**JOBS[0])
+    with pytest.raises(shk.ShakenError):
+        srv.read_job(jid, 64)                   # queued, not running yet
+    srv.tick()
+    s, steps = srv.read_job(jid, 64)
+    assert steps == 2 and s.shape == (64, 64)
+    from paper_1908_07341_gb300 import _lib
+    import ctypes
+    small = np.zeros(64 * 64 - 1, dtype=np.int8)
+    n = ctypes.c_uint64()
+    assert _lib.lib().shk_server_read_job(srv._h, jid, 0, small.ctypes.data, small.size,
+                                          ctypes.byref(n)) == _lib.ENOMEM
+    assert _lib.lib().shk_server_read_job(srv._h, jid + 99, 0, small.ctypes.data, 1 << 20,
+                                          ctypes.byref(n)) == _lib.EINVAL
+    srv.close()
+

@@ -157,6 +157,12 @@ def test_batch_arguments_are_checked_without_a_gpu(so):
     assert b"L=33" in so.shk_last_error(None)
 
 
+def test_server_read_job_argument_checks_without_a_gpu(so):
+    buf = np.zeros(64, dtype=np.int8)
+    steps = ctypes.c_uint64()
+    assert so.shk_server_read_job(None, 1, 0, buf.ctypes.data, buf.size, ctypes.byref(steps)) == _lib.EINVAL
+
+
 def test_checkerboard_argument_checks_without_gpu():
     so = _lib.lib()
     dummy = ctypes.c_void_p(16)
