@@ -250,6 +250,20 @@ int shk_cftp(int dynamics, int n_pairs, const int* L, const double* q, const dou
  * the measured Philox ceiling of the bit-packed draw.  Asynchronous. */
 int shk_philox_peak(int blocks, uint32_t iters, uint32_t* dev_out, void* stream);
 
+/* Bounded waits (no counterpart in the paper).  The int8 sweep variants that
+ * move rows with bulk asynchronous copies (strip-bulk*) wait for each copy on
+ * an mbarrier for at most about two seconds; a wait that gives up sets a
+ * device fault word, lets the launch finish without the rest of its rows and
+ * leaves the output incomplete.  shk_sweep_status synchronises `stream` and
+ * returns SHK_ETIMEOUT (and clears the word) if that happened since the last
+ * check; shk_read_observables and shk_read_spins check it as well.
+ * shk_bulk_wait_timeout_test launches one warp that waits, at most
+ * limit_cycles SM clock cycles (1..2^30), for a barrier no copy will complete,
+ * and reports in *timed_out whether the wait gave up and set the word (it
+ * should): the failure path, exercised without a fault.  Synchronous. */
+int shk_sweep_status(void* stream);
+int shk_bulk_wait_timeout_test(uint32_t limit_cycles, int* timed_out, void* stream);
+
 /* Run-time specialisation of the half-step sweeps (no counterpart in the
  * paper).  The draw of Eqs. leftTrans / rightTrans compares the random bit
  * planes with the bits of the three class thresholds of (q, J); compiled with
@@ -362,8 +376,11 @@ void* shk_plane_ptr(shk_lattice* lat, int plane);
  * paper, which ran one (q, J) point per CPU thread).  One persistent kernel
  * advances every lattice by steps_per_launch full steps per launch: each
  * lattice is cut into tiles of whole rows (about tile_sites sites each); a CTA
- * takes a tile and its halo rows into shared memory and steps it there.  The
- * launch is captured once in a CUDA graph and replayed.  Every lattice follows
+ * takes a tile and its halo rows into shared memory and steps it there.  A
+ * run (shk_batch_run) is one launch of a CUDA graph whose while node repeats
+ * the kernel n_steps / steps_per_launch times (the kernel counts the launches
+ * down on the device; a one-thread kernel before the graph sets the count).
+ * Every lattice follows
  * exactly the trajectory shk_run would give it (same random numbers), and its
  * five sums of every step t >= burn_in are folded into SHK_NSTATS exact int64
  * statistics:

@@ -50,6 +50,8 @@ SIGNATURES = {
     "shk_cftp_scratch_bytes": (_sz, [_i]),
     "shk_philox_peak": (_i, [_i, _u32, _vp, _vp]),
     "shk_debug_bounds": (_i, [_vp]),
+    "shk_sweep_status": (_i, [_vp]),
+    "shk_bulk_wait_timeout_test": (_i, [_u32, _vp, _vp]),
     "shk_set_specialize": (_i, [_i]),
     "shk_get_specialize": (_i, []),
     "shk_specialize_prepare": (_i, [_i, _i, _d, _d, _i]),

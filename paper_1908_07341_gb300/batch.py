@@ -1,9 +1,10 @@
 """Python face of the batched-lattice C ABI (shk_batch_*).
 
 A batch advances many independent bit-packed lattices of uneven side L, each
-with its own (q, J), seed and lattice id, in one persistent kernel replayed
-from a CUDA graph.  The statistics are exact int64 sums; ``derived`` turns
-them into the usual per-lattice averages in FP64.
+with its own (q, J), seed and lattice id, in one persistent kernel; a run is
+one CUDA graph launch whose while node repeats the kernel.  The statistics
+are exact int64 sums; ``derived`` turns them into the usual per-lattice
+averages in FP64.
 """
 from __future__ import annotations
 

@@ -531,6 +531,39 @@ int shk_run(shk_lattice* lat, uint64_t n_steps, int64_t* dev_obs) {
     return SHK_OK;
 }
 
+int shk_sweep_status(void* stream) {
+    bool fault = false;
+    const cudaError_t e = sweep_fault_take(static_cast<cudaStream_t>(stream), &fault);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_sweep_status");
+    if (fault)
+        return fail(nullptr, SHK_ETIMEOUT,
+                    "shk_sweep_status: a sweep's wait on its own row copies gave up; its output is incomplete");
+    return SHK_OK;
+}
+
+int shk_bulk_wait_timeout_test(uint32_t limit_cycles, int* timed_out, void* stream) {
+    if (timed_out == nullptr || limit_cycles == 0 || limit_cycles > (1u << 30))
+        return fail(nullptr, SHK_EINVAL, "shk_bulk_wait_timeout_test: bad argument (limit_cycles in 1..2^30)");
+    *timed_out = 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool fault = false;
+    cudaError_t e = sweep_fault_take(st, &fault);   // start from a clear word
+    if (e == cudaSuccess) e = launch_bulk_wait_probe((long long)limit_cycles, st);
+    if (e == cudaSuccess) e = sweep_fault_take(st, &fault);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "shk_bulk_wait_timeout_test");
+    *timed_out = fault ? 1 : 0;
+    return SHK_OK;
+}
+
+// After a synchronising read: SHK_ETIMEOUT if a sweep's bounded wait gave up.
+static int sweep_fault_status(shk_lattice* lat) {
+    bool fault = false;
+    const cudaError_t e = sweep_fault_take(lat->stream, &fault);
+    if (e != cudaSuccess) return cuda_fail(lat, e, "reading the sweep fault word");
+    if (fault) return fail(lat, SHK_ETIMEOUT, "a sweep's wait on its own row copies gave up; the state is incomplete");
+    return SHK_OK;
+}
+
 int shk_read_observables(shk_lattice* lat, int64_t host_out[SHK_NOBS]) {
     if (lat == nullptr || host_out == nullptr)
         return fail(lat, SHK_EINVAL, "shk_read_observables: NULL argument");
@@ -539,7 +572,7 @@ int shk_read_observables(shk_lattice* lat, int64_t host_out[SHK_NOBS]) {
                                     cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(lat, e, "shk_read_observables");
-    return SHK_OK;
+    return sweep_fault_status(lat);
 }
 
 int shk_read_spins(shk_lattice* lat, int plane, int8_t* host_out) {
@@ -559,7 +592,7 @@ int shk_read_spins(shk_lattice* lat, int plane, int8_t* host_out) {
             for (int64_t u = 0; u < g.N; ++u) host_out[u] = ((words[u >> 5] >> (u & 31)) & 1u) ? 1 : -1;
     }
     if (e != cudaSuccess) return cuda_fail(lat, e, "shk_read_spins");
-    return SHK_OK;
+    return sweep_fault_status(lat);
 }
 
 int shk_write_spins(shk_lattice* lat, int plane, const int8_t* host_in) {

@@ -21,7 +21,9 @@
 // the last tile of a lattice to finish (ticket counter) folds them into exact
 // int64 statistics; the last CTA of the launch advances the device-side step
 // counter and resets the work counter.  No CTA ever waits for another, so a
-// single kernel node can be replayed from a CUDA graph for the whole run.
+// whole run is one CUDA graph launch: a while node whose body is one launch of
+// the kernel, the last CTA of each launch counting the run's launches down and
+// ending the loop after the last.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -69,6 +71,7 @@ struct BatchState {
     unsigned long long launches;   // launches completed
     unsigned int next;             // work counter of the running launch
     unsigned int done;             // CTAs finished in the running launch
+    unsigned int launches_left;    // launches still to run in a graph loop (see loop)
 };
 
 struct BatchArgs {
@@ -80,6 +83,11 @@ struct BatchArgs {
     BatchState* state;
     long long* stats;              // n_lattices x kStatFields
     long long* last_obs;           // n_lattices x 5
+    // Inside the body of a graph's while node: the launch's last CTA counts
+    // launches_left down (never below zero) and keeps the loop running while
+    // it is positive.  Outside a graph loop, loop = 0 and cond is unused.
+    cudaGraphConditionalHandle cond;
+    int loop;
 };
 
 // Global row of local row rho of a tile whose first row is r_base: r_base is
@@ -323,10 +331,19 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
             a.state->next = 0u;
             a.state->done = 0u;
             a.state->launches += 1ull;
+            if (a.loop) {
+                const unsigned int left = a.state->launches_left;
+                const unsigned int now = left > 0u ? left - 1u : 0u;
+                a.state->launches_left = now;
+                cudaGraphSetConditional(a.cond, now > 0u ? 1u : 0u);
+            }
             __threadfence();
         }
     }
 }
+
+// Launch count of the next graph run (one thread).
+__global__ void k_batch_set_launches(BatchState* state, unsigned int launches) { state->launches_left = launches; }
 
 }  // namespace shk
 
@@ -359,7 +376,7 @@ struct shk_batch {
     int block = 256;
     int tile_sites = 1 << 18;
     size_t smem_bytes = 0;
-    // graph of one launch
+    // graph of a whole run: a while node whose body is one launch
     cudaGraphExec_t graph = nullptr;
     std::string err;
 };
@@ -467,8 +484,11 @@ cudaError_t prepare_batch(shk_batch* b, int* grid) {
     }
 }
 
-cudaError_t launch_batch(shk_batch* b, int grid, cudaStream_t st) {
+cudaError_t launch_batch(shk_batch* b, int grid, cudaStream_t st, bool loop = false,
+                         cudaGraphConditionalHandle cond = 0) {
     BatchArgs args;
+    args.cond = cond;
+    args.loop = loop ? 1 : 0;
     args.arena = b->dev;
     args.lat = reinterpret_cast<BatchLattice*>(b->dev + b->off_lat);
     args.items = reinterpret_cast<const BatchItem*>(b->dev + b->off_items);
@@ -666,30 +686,48 @@ int shk_batch_run(shk_batch* b, uint64_t n_steps, uint64_t burn_in) {
     }
     cudaError_t e;
     if (b->graph == nullptr) {
+        // One graph for the whole run: a while node whose body is one launch
+        // of the persistent kernel; the kernel ends the loop once the
+        // device-side launch count is used up.
         int grid = 0;
         e = prepare_batch(b, &grid);
         if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run: %s", cudaGetErrorString(e));
-        cudaStream_t cap;
-        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run: %s", cudaGetErrorString(e));
         cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        cudaStream_t cap = nullptr;
+        e = cudaGraphCreate(&g, 0);
+        cudaGraphConditionalHandle cond = 0;
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const cudaError_t le = launch_batch(b, grid, cap);
-            e = cudaStreamEndCapture(cap, &g);
+            const cudaError_t le = launch_batch(b, grid, cap, true, cond);
+            cudaGraph_t body = nullptr;
+            e = cudaStreamEndCapture(cap, &body);
             if (le != cudaSuccess) e = le;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
         if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cap);
+        if (cap) cudaStreamDestroy(cap);
         if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run graph: %s", cudaGetErrorString(e));
     }
-    for (uint64_t s = 0; s < n_steps; s += (uint64_t)b->k) {
-        e = cudaGraphLaunch(b->graph, b->stream);
-        if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run launch: %s", cudaGetErrorString(e));
-        b->step += (uint64_t)b->k;
-        b->parity ^= 1u;
-    }
+    // the run's launch count (stored on the device by a one-thread kernel, so
+    // that the call stays asynchronous), then one graph launch for all of them
+    const unsigned int launches = (unsigned int)(n_steps / (uint64_t)b->k);
+    k_batch_set_launches<<<1, 1, 0, b->stream>>>(reinterpret_cast<BatchState*>(b->dev + b->off_state), launches);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_run launch: %s", cudaGetErrorString(e));
+    b->step += n_steps;
+    b->parity ^= launches & 1u;
     return SHK_OK;
 }
 

@@ -33,6 +33,17 @@ __device__ __forceinline__ T* checked(T* base, uint64_t i, uint64_t n, unsigned 
     return base + i;
 }
 
+// The len elements base[i .. i + len) (a bulk copy's source): checked as a
+// whole, replaced by the buffer's start when they do not fit.
+template <class T>
+__device__ __forceinline__ T* checked_range(T* base, uint64_t i, uint64_t len, uint64_t n, unsigned site) {
+    if (i + len > n || len > n) {
+        atomicCAS(&g_bounds_site, 0u, site);
+        return base;
+    }
+    return base + i;
+}
+
 #ifndef __CUDACC_RTC__
 // First recorded site of this translation unit (0 = none), cleared.
 static inline unsigned take_bounds_site() {
@@ -46,6 +57,10 @@ constexpr bool kBoundsChecked = true;
 #else
 template <class T>
 __device__ __forceinline__ T* checked(T* base, uint64_t i, uint64_t, unsigned) {
+    return base + i;
+}
+template <class T>
+__device__ __forceinline__ T* checked_range(T* base, uint64_t i, uint64_t, uint64_t, unsigned) {
     return base + i;
 }
 #ifndef __CUDACC_RTC__

@@ -429,6 +429,77 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ---------------------------------------------------------------- bulk copies
+//
+// Blackwell bulk asynchronous copies (cp.async.bulk, the tensor memory
+// accelerator's untiled form): one thread moves a contiguous range of global
+// memory (16-byte aligned, a multiple of 16 bytes) into shared memory, and
+// the transfer signals completion on an mbarrier in shared memory by its byte
+// count.  Waiting threads poll the barrier's phase; every wait here is
+// bounded.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes barrier initialisation visible to the asynchronous copy engine.
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The calling thread's arrival, announcing `bytes` more to be transferred in
+// the barrier's current phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(smem_dst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.b32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity), "r"(1000u) : "memory");
+    return done != 0u;
+}
+
+// Non-blocking check of the same phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.b32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return done != 0u;
+}
+
+// Waits until the barrier's phase with the given parity has completed, for at
+// most limit_cycles SM clock cycles (and 2^24 polls): false if it gave up.
+// A phase that has already completed (the common case, copies being staged
+// rows ahead) is seen by one non-blocking test.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit_cycles) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t n = 0; n < (1u << 24); ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > limit_cycles) return false;
+    }
+    return false;
+}
+
+// Poll limit of the sweeps' waits on their own copies: about two seconds at
+// the maximum SM clock, far beyond any transfer that is still making progress.
+constexpr long long kCopyWaitCycles = 4000000000LL;
+
 // ---------------------------------------------------------------- division
 
 // Division by a fixed divisor d >= 1 for n < 2^31: q = (umulhi(n, m) + n) >> s

@@ -89,6 +89,13 @@ cudaError_t launch_run_small(const Geometry& g, void* sigma, void* tau, const Dr
                              uint64_t t0, uint64_t n, long long* obs, long long* last,
                              cudaStream_t st);
 
+// Fault word of the sweeps' bounded waits on their own bulk copies: its
+// device address, a synchronising read-and-clear, and a probe kernel whose
+// wait cannot complete (the failure path, tested without a fault).
+cudaError_t sweep_fault_word(unsigned int** out);
+cudaError_t sweep_fault_take(cudaStream_t st, bool* fault);
+cudaError_t launch_bulk_wait_probe(long long limit_cycles, cudaStream_t st);
+
 // True when p is 16-byte aligned (the sweeps use 16-byte vector accesses).
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }

@@ -261,6 +261,56 @@ static PhiloxPrefix philox_prefix(const DrawParams& P, uint32_t hs, int c) {
     return u;
 }
 
+// Set non-zero by a sweep whose bounded wait on its own copies gave up; read
+// and cleared by sweep_fault_take (shk_sweep_status and the lattice reads).
+__device__ unsigned int g_sweep_fault;
+
+// Device address of the fault word on the current device, looked up at each
+// use (cheap next to a launch), so that it never outlives its context.
+cudaError_t sweep_fault_word(unsigned int** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sweep_fault);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<unsigned int*>(p);
+    return cudaSuccess;
+}
+
+// Reads and clears the fault word after synchronising `st`: true if a wait
+// gave up since the last call.
+cudaError_t sweep_fault_take(cudaStream_t st, bool* fault) {
+    unsigned int v = 0;
+    const unsigned int zero = 0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_sweep_fault, sizeof v);
+    if (e == cudaSuccess && v != 0u) e = cudaMemcpyToSymbol(g_sweep_fault, &zero, sizeof zero);
+    *fault = v != 0u;
+    return e;
+}
+
+// One warp arms an mbarrier for 16 bytes that no copy will deliver and waits
+// for it, bounded by limit_cycles: the wait gives up, the kernel sets the
+// fault word and returns.  Nothing is in flight, so nothing else happens.
+__global__ void k_bulk_wait_probe(unsigned int* fault, long long limit_cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar, 16u);
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar, 0u, limit_cycles));
+    if (!ok && threadIdx.x == 0) atomicOr(fault, 1u);
+}
+
+cudaError_t launch_bulk_wait_probe(long long limit_cycles, cudaStream_t st) {
+    unsigned int* f = nullptr;
+    cudaError_t e = sweep_fault_word(&f);
+    if (e != cudaSuccess) return e;
+    k_bulk_wait_probe<<<1, 32, 0, st>>>(f, limit_cycles);
+    return cudaGetLastError();
+}
+
 SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawParams& P,
                      uint32_t hs, long long* oc, long long* op, long long* z) {
     SweepArgs a;
@@ -277,6 +327,7 @@ SweepArgs sweep_args(const Geometry& g, const void* src, void* dst, const DrawPa
     a.zero_slot = z;
     a.P = P;
     for (int c = 0; c < 8; ++c) a.pre[c] = philox_prefix(P, hs, c);
+    a.fault = nullptr;
     return a;
 }
 
@@ -293,6 +344,7 @@ struct SweepVariant {
     const char* name;
     const char* jit[2]; // the same kernels as name expressions for run-time compilation (jit.cu), or null
     int waves;          // grid: at most this many full waves of resident blocks
+    bool bulk;          // moves rows with bounded waits on bulk copies: gets the fault word
 };
 
 #define SHK_JIT_NAMES(kernel, args) {"shk::" #kernel "<0, " args ">", "shk::" #kernel "<1, " args ">"}
@@ -326,6 +378,8 @@ static const SweepVariant kI8Variants[] = {
      "strip-async2-256x3", SHK_JIT_NAMES(k_sweep_strip_async, "2, 256, 3, 2")},
     {{k_sweep_strip_async<0, kInt8, 256, 3, 2>, k_sweep_strip_async<1, kInt8, 256, 3, 2>}, 256, 32,
      "strip-async2-256x3-w2", SHK_JIT_NAMES(k_sweep_strip_async, "2, 256, 3, 2"), 2},
+    {{k_sweep_strip_bulk<0, 256, 3, 4>, k_sweep_strip_bulk<1, 256, 3, 4>}, 256, 32, "strip-bulk4-256x3",
+     SHK_JIT_NAMES(k_sweep_strip_bulk, "256, 3, 4"), 1, true},
     {{k_sweep_strip<0, kInt8, 256, 3>, k_sweep_strip<1, kInt8, 256, 3>}, 256, 32, "strip-256x3",
      SHK_JIT_NAMES(k_sweep_strip, "2, 256, 3")},
     {{k_sweep_q<0, kInt8, 256, 3>, k_sweep_q<1, kInt8, 256, 3>}, 256, 1, "queue-256x3",
@@ -338,7 +392,7 @@ static const SweepVariant kI8Variants[] = {
 constexpr int kNumBpVariants = sizeof(kBpVariants) / sizeof(kBpVariants[0]);
 constexpr int kNumI8Variants = sizeof(kI8Variants) / sizeof(kI8Variants[0]);
 constexpr int kBpRowFallback = 3;   // variant used when rows are too short for the chosen one (queue-256x3)
-constexpr int kI8RowFallback = 3;
+constexpr int kI8RowFallback = 4;
 
 static std::atomic<int> g_bp_variant{0};
 static std::atomic<int> g_i8_variant{0};
@@ -390,6 +444,10 @@ cudaError_t launch_halfstep(const Geometry& g, int half, const void* src, void* 
         const SweepVariant& v = table[vi];
         cudaError_t e = cudaSuccess;
         const int waves = v.waves > 0 ? v.waves : 1;
+        if (v.bulk) {
+            const cudaError_t fe = sweep_fault_word(&a.fault);
+            if (fe != cudaSuccess) return fe;
+        }
         if (jit_launch(v.jit[0], v.jit[1], v.block, half, g.nblocks, a, st, &e, loaded_only, waves)) return e;
         SweepKernel k = v.k[half];
         return launch_pdl(k, grid_for(k, v.block, g.nblocks, waves), v.block, st, a);

@@ -29,6 +29,7 @@ struct SweepArgs {
     long long* zero_slot;
     DrawParams P;
     PhiloxPrefix pre[8];  // round prefixes of the 8 Philox calls of half-step hs
+    unsigned int* fault;  // set non-zero by a kernel whose bounded wait gave up (nullable)
 };
 
 // Programmatic dependent launch: the kernels are launched so that the next

@@ -699,6 +699,164 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
     finish_step<HALF>(acc, a);
 }
 
+// int8 strip walk with the rows moved by bulk asynchronous copies: a strip's
+// row is 32 blocks of 32 bytes, 1024 contiguous bytes, so lane 0 stages the
+// whole row with one cp.async.bulk (plus one 16-byte copy of the aligned
+// chunk that holds the strip-edge byte), DEPTH rows ahead, into a per-warp
+// ring whose slots complete on their own mbarrier.  The lanes wait for the
+// slot's phase, unpack their 32 bytes and continue as k_sweep_strip_async.
+// A wait that gives up (kCopyWaitCycles) sets *a.fault, waits (bounded) for
+// the warp's copies still in flight and skips the rest of the warp's rows;
+// the launch still completes, and the host reports the fault.
+template <int HALF, int BLOCK, int MINB, int DEPTH>
+__global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArgs a) {
+    pdl_begin();
+    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    __shared__ __align__(128) uint32_t ring[BLOCK / 32][DEPTH][256];       // 1024 bytes per row
+    __shared__ __align__(16) uint32_t ring_edge[BLOCK / 32][DEPTH][4];     // the edge word (first of 4)
+    __shared__ __align__(8) uint64_t bar[BLOCK / 32][DEPTH];
+    const DrawParams& P = a.P;
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t (*q)[kQueueCap] = qbuf[wib];
+    if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
+    const bool cnn = HALF == 0 && a.obs_prev != nullptr;
+    int acc[4] = {0, 0, 0, 0};
+    uint32_t head = 0;
+    int count = 0;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t W = a.Wr, L = a.L;
+    const uint32_t nstrips = W / 32;
+    const bool edge_lane = HALF == 0 ? lane == 0 : lane == 31;
+    const unsigned char* src8 = static_cast<const unsigned char*>(a.src);
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) mbar_init(&bar[wib][d], 1);
+        mbar_fence_init();
+    }
+    __syncwarp();
+    uint32_t seq = 0;          // rows staged by this warp before the current task (slot = seq % DEPTH)
+    bool failed = false;
+    const uint64_t total = (uint64_t)nstrips * L;
+    uint64_t pos = total * gwarp / nwarps;
+    const uint64_t end = total * (gwarp + 1) / nwarps;
+    while (pos < end && !failed) {
+        const uint32_t strip = (uint32_t)(pos / L);
+        const uint32_t r0 = (uint32_t)(pos - (uint64_t)strip * L);
+        const uint64_t left_here = end - pos, left_in_strip = L - r0;
+        const uint32_t nrows = (uint32_t)(left_here < left_in_strip ? left_here : left_in_strip);
+        pos += nrows;
+        const uint32_t col = strip * 32 + lane;
+        const uint32_t edge_block = HALF == 0 ? (strip == 0 ? W - 1 : strip * 32 - 1)
+                                              : (strip + 1 == nstrips ? 0 : strip * 32 + 32);
+        auto row_at = [&](uint32_t i) -> uint32_t { return HALF == 0 ? r0 + i : r0 + nrows - 1 - i; };
+        // row i of the walk goes to slot (seq + i) % DEPTH: lane 0 stages the
+        // strip's 1024 bytes with one bulk copy, the edge lane the 4-byte word
+        // holding the byte next to the strip with cp.async (one group per
+        // lane and row, committed by every lane)
+        auto stage = [&](uint32_t i) {
+            if (i < nrows) {
+                const uint32_t r = row_at(i), sl = (seq + i) % DEPTH;
+                if (lane == 0) {
+                    const size_t row_byte = (size_t)r * L;
+                    // the lanes' reads of this slot (generic proxy) come
+                    // before the copy engine's writes to it
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive_expect_tx(&bar[wib][sl], 1024u);
+                    bulk_g2s(&ring[wib][sl][0],
+                             checked_range(src8, row_byte + (size_t)strip * 1024, 1024, 32 * (uint64_t)a.nblocks,
+                                           SHK_SITE),
+                             1024u, &bar[wib][sl]);
+                }
+                if (edge_lane) {
+                    const size_t eb = (size_t)r * W + edge_block;
+                    const uint32_t* q1 = reinterpret_cast<const uint32_t*>(a.src);
+                    cp_async4(&ring_edge[wib][sl][0],
+                              checked(q1, 8 * eb + (HALF == 0 ? 7 : 0), 8 * (uint64_t)a.nblocks, SHK_SITE));
+                }
+            }
+            cp_async_commit();
+        };
+        const uint32_t first = row_at(0);
+        const uint32_t nb_row = HALF == 0 ? (first == 0 ? L - 1 : first - 1) : (first + 1 == L ? 0 : first + 1);
+        uint32_t prev = row_bits<kInt8>(load_row<kInt8>(a.src, nb_row * W + col, a.nblocks));
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) stage(d);
+        uint32_t i = 0;
+        for (; i < nrows; ++i) {
+            const uint32_t row = row_at(i), sl = (seq + i) % DEPTH, par = ((seq + i) / DEPTH) & 1u;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[wib][sl], par, kCopyWaitCycles));
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            cp_async_wait<DEPTH - 1>();      // the edge lane's word of row i has landed
+            const uint32_t* slot = &ring[wib][sl][lane * 8];
+            const uint4 lo = *reinterpret_cast<const uint4*>(slot);
+            const uint4 hi = *reinterpret_cast<const uint4*>(slot + 4);
+            const uint32_t S = pack_up32(lo, hi);
+            uint32_t edge = 0;
+            if (edge_lane) {
+                const uint32_t e = ring_edge[wib][sl][0];
+                edge = HALF == 0 ? (uint32_t)((int8_t)(e >> 24) > 0) : (uint32_t)((int8_t)(e & 0xFFu) > 0);
+            }
+            __syncwarp();                    // every lane has read the slot before it is refilled
+            stage(i + DEPTH);
+            const uint32_t N1 = prev;
+            uint32_t N2;
+            if (HALF == 0) {
+                const uint32_t left = __shfl_up_sync(0xffffffffu, S, 1) >> 31;
+                N2 = (S << 1) | (lane == 0 ? edge : left);
+            } else {
+                const uint32_t right = __shfl_down_sync(0xffffffffu, S, 1) & 1u;
+                N2 = (S >> 1) | ((lane == 31 ? edge : right) << 31);
+            }
+            const uint32_t w = row * W + col;
+            const BlockClass k = block_class(S, N1, N2);
+            uint32_t und, up;
+            draw_first_two_pre(k, w, 0xffffffffu, a.pre, P, und, up);
+            const bool parked = und != 0u;
+            const uint32_t mask = __ballot_sync(0xffffffffu, parked);
+            if (parked) {
+                const uint32_t qi = (head + count + __popc(mask & below)) & (kQueueCap - 1);
+                q[0][qi] = w;
+                q[1][qi] = und;
+                q[2][qi] = up;
+                q[3][qi] = S;
+                q[4][qi] = N1;
+                q[5][qi] = N2;
+            } else {
+                finish_block<HALF, kInt8>(a, w, up, S, N1, N2, cnn, acc);
+            }
+            count += __popc(mask);
+            if (count >= 32) {
+                __syncwarp();
+                drain_queue<HALF, kInt8>(a, P, q, head, 32, cnn, acc);
+                __syncwarp();
+                head = (head + 32) & (kQueueCap - 1);
+                count -= 32;
+            }
+            prev = S;
+        }
+        if (failed) {
+            // the rows staged but not consumed: wait (bounded) for their copies,
+            // so that none still writes to the ring when the block exits
+            for (uint32_t j = i; j < nrows && j < i + DEPTH; ++j)
+                (void)mbar_wait_bounded(&bar[wib][(seq + j) % DEPTH], ((seq + j) / DEPTH) & 1u, kCopyWaitCycles);
+            if (lane == 0 && a.fault != nullptr) atomicOr(a.fault, 1u);
+        }
+        cp_async_wait<0>();                  // no edge copy may still target the ring
+        __syncwarp();
+        seq += nrows;
+    }
+    if (count > 0) {
+        __syncwarp();
+        drain_queue<HALF, kInt8>(a, P, q, head, count, cnn, acc);
+    }
+    finish_step<HALF>(acc, a);
+}
+
 // int8 half-step for any L (site-by-site neighbour gathers; partial last block).
 template <int HALF>
 __global__ void __launch_bounds__(256) k_sweep_i8g(const SweepArgs a) {

@@ -157,6 +157,13 @@ def test_batch_arguments_are_checked_without_a_gpu(so):
     assert b"L=33" in so.shk_last_error(None)
 
 
+def test_bulk_wait_timeout_test_argument_checks_without_a_gpu(so):
+    flag = np.zeros(1, dtype=np.int32)
+    assert so.shk_bulk_wait_timeout_test(0, flag.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_bulk_wait_timeout_test((1 << 30) + 1, flag.ctypes.data, None) == _lib.EINVAL
+    assert so.shk_bulk_wait_timeout_test(1000, None, None) == _lib.EINVAL
+
+
 def test_server_read_job_argument_checks_without_a_gpu(so):
     buf = np.zeros(64, dtype=np.int8)
     steps = ctypes.c_uint64()
