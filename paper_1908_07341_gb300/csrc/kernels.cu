@@ -362,6 +362,8 @@ static const SweepVariant kBpVariants[] = {
      SHK_JIT_NAMES(k_sweep_q, "1, 256, 3")},
     {{k_sweep_qv<0, 2, 256, 3>, k_sweep_qv<1, 2, 256, 3>}, 256, 2, "queue-v2-256x3",
      SHK_JIT_NAMES(k_sweep_qv, "2, 256, 3")},
+    {{k_sweep_qv<0, 4, 256, 2>, k_sweep_qv<1, 4, 256, 2>}, 256, 4, "queue-v4-256x2",
+     SHK_JIT_NAMES(k_sweep_qv, "4, 256, 2")},
     {{k_sweep_strip_async<0, kBitpack, 256, 3, 4>, k_sweep_strip_async<1, kBitpack, 256, 3, 4>}, 256, 32,
      "strip-async4-256x3", SHK_JIT_NAMES(k_sweep_strip_async, "1, 256, 3, 4")},
     {{k_sweep_strip<0, kBitpack, 256, 3>, k_sweep_strip<1, kBitpack, 256, 3>}, 256, 32, "strip-256x3",

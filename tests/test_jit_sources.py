@@ -78,10 +78,11 @@ def _compile(nv, names, U):
 def test_variant_tables_name_specialised_forms():
     names = _name_expressions()
     # distinct kernels; bit-packed: queue-v4 (one, two or four waves), queue x3, queue-v2,
-    # strip-async, strip, queue-128, queue x4; int8: strip-async (one or two waves), strip-bulk,
+    # queue-v4 x2, strip-async, strip, queue-128, queue x4; int8: strip-async (one or two waves), strip-bulk,
     # strip, queue x2
-    assert len(names) == 2 * 12
+    assert len(names) == 2 * 13
     assert "shk::k_sweep_strip_bulk<0, 256, 3, 4>" in names
+    assert "shk::k_sweep_qv<1, 4, 256, 2>" in names
     assert "shk::k_sweep_q<0, 1, 256, 3>" in names
     assert "shk::k_sweep_strip_async<1, 2, 256, 3, 2>" in names
 
