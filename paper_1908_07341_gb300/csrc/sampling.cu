@@ -155,6 +155,21 @@ __device__ __forceinline__ void pair_reset(const PairPlanes& p) {
     __syncthreads();
 }
 
+// The four planes of call c for one chain of a coupled pair, accumulating
+// the decided-up sites directly (up |= und & ~x & g); the same comparison as
+// apply_planes, in the form that measured faster for the two-chain draw.
+__device__ __forceinline__ void apply_planes_up(const uint4& R, int c, const BlockClass& k, uint32_t& und,
+                                                uint32_t& up, const DrawParams& P) {
+    const uint32_t x[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int b = 4 * c + m;
+        const uint32_t g = k.F ^ SHK_PLANE_M0(P, b) ^ (k.Cg & SHK_PLANE_D01(P, b)) ^ (k.C2 & SHK_PLANE_D12(P, b));
+        up |= und & ~x[m] & g;
+        und &= ~(x[m] ^ g);
+    }
+}
+
 // Draws block w of both coupled chains from one set of uniforms: each Philox
 // call (four planes) serves the two chains, and the lazy loop ends when
 // neither has an undecided site in the warp.  All 32 lanes call it together.
@@ -165,12 +180,13 @@ __device__ __forceinline__ void draw_coupled(const BlockClass (&k)[2], uint32_t 
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const uint4 R = philox_call(w, hs, c, P);
-        apply_planes(R, c, k[0], und[0], up[0], P);
-        apply_planes(R, c, k[1], und[1], up[1], P);
+        apply_planes_up(R, c, k[0], und[0], up[0], P);
+        apply_planes_up(R, c, k[1], und[1], up[1], P);
         if (c < 7 && !__any_sync(0xffffffffu, (und[0] | und[1]) != 0u)) break;
     }
-    up[0] = draw_result(und[0], up[0], k[0].F);
-    up[1] = draw_result(und[1], up[1], k[1].F);
+    // ties through all 32 planes: a + site stays -1, a - site comes out +1
+    up[0] |= und[0] & k[0].F;
+    up[1] |= und[1] & k[1].F;
 }
 
 // One full step with index t of both chains, driven by the same uniforms
