@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArg
     pdl_begin();
     __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
     __shared__ __align__(128) uint32_t ring[BLOCK / 32][DEPTH][256];       // 1024 bytes per row
-    __shared__ __align__(16) uint32_t ring_edge[BLOCK / 32][DEPTH][4];     // the edge word (first of 4)
+    __shared__ uint32_t ring_edge[BLOCK / 32][DEPTH];                      // the word holding the edge byte
     __shared__ __align__(8) uint64_t bar[BLOCK / 32][DEPTH];
     const DrawParams& P = a.P;
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArg
                 if (edge_lane) {
                     const size_t eb = (size_t)r * W + edge_block;
                     const uint32_t* q1 = reinterpret_cast<const uint32_t*>(a.src);
-                    cp_async4(&ring_edge[wib][sl][0],
+                    cp_async4(&ring_edge[wib][sl],
                               checked(q1, 8 * eb + (HALF == 0 ? 7 : 0), 8 * (uint64_t)a.nblocks, SHK_SITE));
                 }
             }
@@ -798,7 +798,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArg
             const uint32_t S = pack_up32(lo, hi);
             uint32_t edge = 0;
             if (edge_lane) {
-                const uint32_t e = ring_edge[wib][sl][0];
+                const uint32_t e = ring_edge[wib][sl];
                 edge = HALF == 0 ? (uint32_t)((int8_t)(e >> 24) > 0) : (uint32_t)((int8_t)(e & 0xFFu) > 0);
             }
             __syncwarp();                    // every lane has read the slot before it is refilled

@@ -193,6 +193,54 @@ def _check_16384(orc, layout, L, q, J, seed, T):
         assert np.array_equal(obs, orc.observables(s_new, t_new, L)), target
 
 
+def _plane_rows(plane, layout, L, rows):
+    """int8 +/-1 copies of some rows of a device plane (only those rows leave the device)."""
+    idx = torch.tensor(rows, dtype=torch.long, device=plane.device)
+    if layout == "bitpack":
+        words = plane[: L * L // 8].view(torch.int32).view(L, L // 32).index_select(0, idx).cpu().numpy()
+        bits = (words.view(np.uint32)[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1
+        vals = (2 * bits.astype(np.int8) - 1).reshape(len(rows), L)
+    else:
+        vals = plane[: L * L].view(torch.int8).view(L, L).index_select(0, idx).cpu().numpy()
+    return {r: vals[k] for k, r in enumerate(rows)}
+
+
+@pytest.mark.parametrize("layout,L", [("bitpack", 65536), ("int8", 32768)])
+def test_largest_planes_sampled(orc, layout, L):
+    """Planes far beyond the benchmark's 16384^2: 2^32 sites per sublattice
+    bit-packed (block indices up to 2^27) and 2^30 int8, in the default launch
+    shape.  After one step from a random start, the oracle recomputes step 1
+    (Eqs. leftTrans / rightTrans) from the GPU's own state on row bands that
+    include both wrap-around rows and the middle of the torus.  Only the
+    needed rows are copied to the host; the oracle gets them in a full-size
+    array that is otherwise never touched."""
+    q, J, seed, lid = 0.9, 0.4, 11, 5
+    T = orc.thresholds(q, J)
+    lat = shk.Lattice(L, layout).set_seed(seed, lid).set_params(q, J).init("random", init_seed=3)
+    lat.run(1)
+    bands = [(0, 2), (L // 2 - 1, L // 2 + 1), (L - 2, L)]
+    around = sorted({r % L for r0, r1 in bands for r in range(r0 - 1, r1 + 1)})
+    sigma0 = _plane_rows(lat.plane(0), layout, L, around)
+    lat.run(1)
+    tau1 = _plane_rows(lat.plane(1), layout, L, around)
+    sigma1 = _plane_rows(lat.plane(0), layout, L, around)
+    src = np.zeros(L * L, dtype=np.int8)
+    dst = np.zeros(L * L, dtype=np.int8)
+    for r, v in sigma0.items():
+        src[r * L:(r + 1) * L] = v
+    for r0, r1 in bands:
+        orc.halfstep(0, src, L, T, seed, lid, 2, r0, r1, dst=dst)
+        for r in range(r0, r1):
+            assert np.array_equal(dst[r * L:(r + 1) * L], tau1[r]), ("tau", r)
+    for r, v in tau1.items():
+        src[r * L:(r + 1) * L] = v
+    for r0, r1 in bands:
+        orc.halfstep(1, src, L, T, seed, lid, 3, r0, r1, dst=dst)
+        for r in range(r0, r1):
+            assert np.array_equal(dst[r * L:(r + 1) * L], sigma1[r]), ("sigma", r)
+    lat.close()
+
+
 @pytest.mark.parametrize("L", [64, 96, 288, 1024])
 def test_layouts_give_identical_trajectories(L):
     """The random numbers depend on the site index only, so the bit-packed and
