@@ -100,18 +100,37 @@ __device__ __forceinline__ uint32_t global_row(int32_t r_base, uint32_t rho, uin
     return (uint32_t)g;
 }
 
+// Geometry of one tile in shared memory: R local rows of Wr words (rows
+// wrapping when the tile is the whole torus), local row 0 at global row
+// r_base, and the tile's own rows [own_lo, own_lo + Hloc).
+struct TileGeom {
+    uint32_t R;
+    bool wrap;
+    uint32_t Wr;
+    FastDiv dw;
+    uint32_t L;
+    int32_t r_base;
+    uint32_t own_lo, Hloc;
+};
+
 // Draws rows [rlo, rhi) of dst (local row index) from src in shared memory.
-// HALF 0 reads the row below (rho - 1), HALF 1 the row above (rho + 1); the
-// left/right neighbour wraps within the row.  Random numbers use the global
-// block index (global row g = (r_base + rho) mod L).
-template <int HALF, int BLOCK>
+// HALF 0 reads the row below
+// (rho - 1), HALF 1 the row above (rho + 1); the left/right neighbour wraps
+// within the row.  Random numbers use the global block index (global row
+// g = (r_base + rho) mod L).
+// ROWS: the lattice's rows are whole multiples of 32 words (L a multiple of
+// 1024), so the 32 lanes of a warp always cover 32 consecutive words of one
+// row: the row, its neighbour row and its global row are the same for the
+// whole warp and advance by a fixed stride, with no per-word division and
+// every lane holding a valid block.  Otherwise a warp's 32 words may span
+// rows and the tile's end.
+template <int HALF, int BLOCK, bool ROWS>
 __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, uint32_t rlo, uint32_t rhi,
-                                           uint32_t R, bool wrap, uint32_t Wr, const FastDiv& dw, uint32_t L,
-                                           int32_t r_base, uint32_t hs, const DrawParams& P,
-                                           const PhiloxPrefix (&pre)[8], uint32_t (*q)[kQueueCap]) {
+                                           const TileGeom& g, const DrawParams& P, const PhiloxPrefix (&pre)[8],
+                                           uint32_t (*q)[kQueueCap]) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lo = rlo * Wr, hi = rhi * Wr;
     const uint32_t below = (1u << lane) - 1u;
+    const uint32_t Wr = g.Wr, R = g.R;
     uint32_t head = 0;
     int count = 0;
     auto drain = [&](int n) {
@@ -124,33 +143,18 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
         const uint32_t res = draw_rest_pre(block_class(S, N1, N2), w, und, up, pre, P);
         if (has) dst[i] = res;
     };
-    for (uint32_t base = lo + warp * 32; base < hi; base += BLOCK) {
-        const uint32_t i = base + lane;
-        const bool in = i < hi;
-        uint32_t S = 0, N1 = 0, N2 = 0, w = 0;
-        if (in) {
-            const uint32_t rho = fdiv(i, dw), c = i - rho * Wr;
-            S = src[i];
-            if (HALF == 0) {
-                N1 = src[(rho == 0 && wrap ? R - 1 : rho - 1) * Wr + c];
-                const uint32_t prev = src[rho * Wr + (c == 0 ? Wr - 1 : c - 1)];
-                N2 = (S << 1) | (prev >> 31);
-            } else {
-                N1 = src[(rho + 1 == R && wrap ? 0 : rho + 1) * Wr + c];
-                const uint32_t next = src[rho * Wr + (c + 1 == Wr ? 0 : c + 1)];
-                N2 = (S >> 1) | (next << 31);
-            }
-            w = (uint32_t)global_row(r_base, rho, L) * Wr + c;
-        }
+    // phase 1 of the warp's 32 blocks (block i of lane: local word i, Philox
+    // block w); blocks with undecided sites wait in the queue
+    auto visit = [&](uint32_t i, uint32_t S, uint32_t N1, uint32_t N2, uint32_t w, uint32_t valid) {
         const BlockClass k = block_class(S, N1, N2);
         uint32_t und, up;
-        draw_first_two_pre(k, w, in ? 0xffffffffu : 0u, pre, P, und, up);
+        draw_first_two_pre(k, w, valid, pre, P, und, up);
         const bool parked = und != 0u;
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {
             const uint32_t e = (head + count + __popc(mask & below)) & (kQueueCap - 1);
             q[0][e] = w; q[1][e] = und; q[2][e] = up; q[3][e] = S; q[4][e] = N1; q[5][e] = N2; q[6][e] = i;
-        } else if (in) {
+        } else if (valid != 0u) {
             dst[i] = up;
         }
         count += __popc(mask);
@@ -161,6 +165,60 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
             head = (head + 32) & (kQueueCap - 1);
             count -= 32;
         }
+    };
+    if constexpr (ROWS) {
+        // this warp's first word (rlo, 0) + 32 warp and the stride of BLOCK words
+        const uint32_t f = warp * 32u, dr = fdiv((uint32_t)BLOCK, g.dw), dc = (uint32_t)BLOCK - dr * Wr;
+        uint32_t rho = rlo + fdiv(f, g.dw);
+        uint32_t c0 = f - (rho - rlo) * Wr;
+        while (rho < rhi) {
+            // The lattice's draw parameters stay in shared memory, read where
+            // used: held in registers across iterations they would cost a
+            // third of the CTAs an SM can hold.
+            asm volatile("" ::: "memory");
+            const uint32_t c = c0 + lane, row = rho * Wr, i = row + c;
+            const uint32_t S = src[i];
+            uint32_t N1, N2;
+            if (HALF == 0) {
+                N1 = src[(rho == 0 && g.wrap ? (R - 1) * Wr : row - Wr) + c];
+                const uint32_t prev = src[row + (c == 0 ? Wr - 1 : c - 1)];
+                N2 = (S << 1) | (prev >> 31);
+            } else {
+                N1 = src[(rho + 1 == R && g.wrap ? 0 : row + Wr) + c];
+                const uint32_t next = src[row + (c + 1 == Wr ? 0 : c + 1)];
+                N2 = (S >> 1) | (next << 31);
+            }
+            visit(i, S, N1, N2, global_row(g.r_base, rho, g.L) * Wr + c, 0xffffffffu);
+            c0 += dc;
+            rho += dr;
+            if (c0 >= Wr) {
+                c0 -= Wr;
+                ++rho;
+            }
+        }
+    } else {
+        const uint32_t lo = rlo * Wr, hi = rhi * Wr;
+        for (uint32_t base = lo + warp * 32; base < hi; base += BLOCK) {
+            const uint32_t i = base + lane;
+            const bool in = i < hi;
+            uint32_t S = 0, N1 = 0, N2 = 0, w = 0;
+            if (in) {
+                const uint32_t rho = fdiv(i, g.dw);
+                const uint32_t c = i - rho * Wr;
+                S = src[i];
+                if (HALF == 0) {
+                    N1 = src[(rho == 0 && g.wrap ? R - 1 : rho - 1) * Wr + c];
+                    const uint32_t prev = src[rho * Wr + (c == 0 ? Wr - 1 : c - 1)];
+                    N2 = (S << 1) | (prev >> 31);
+                } else {
+                    N1 = src[(rho + 1 == R && g.wrap ? 0 : rho + 1) * Wr + c];
+                    const uint32_t next = src[rho * Wr + (c + 1 == Wr ? 0 : c + 1)];
+                    N2 = (S >> 1) | (next << 31);
+                }
+                w = global_row(g.r_base, rho, g.L) * Wr + c;
+            }
+            visit(i, S, N1, N2, w, in ? 0xffffffffu : 0u);
+        }
     }
     if (count > 0) {
         __syncwarp();
@@ -168,8 +226,77 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
     }
 }
 
+// Raw counts of one step over the tile's own rows (sigma in sg, tau in tu,
+// both after the step): v[0] = up sites of sigma, v[1] = up sites of tau,
+// v[2] = sites where sigma and tau disagree, v[3] = sigma sites that
+// disagree with tau's up and right neighbours, v[4] = sigma sites that
+// disagree with sigma's up and right neighbours.  ROWS as in tile_sweep: a
+// warp reads 32 words of one row at a time.
+template <int BLOCK, bool ROWS>
+__device__ __forceinline__ void tile_counts(const uint32_t* sg, const uint32_t* tu, const TileGeom& g,
+                                            int (&v)[kNumObs]) {
+    const uint32_t Wr = g.Wr;
+    auto add = [&](uint32_t x, uint32_t xu, uint32_t xr) {
+        const uint32_t s = sg[x], t = tu[x];
+        const uint32_t sU = sg[xu], tU = tu[xu];
+        const uint32_t sR = (s >> 1) | (sg[xr] << 31), tR = (t >> 1) | (tu[xr] << 31);
+        v[0] += __popc(s);
+        v[1] += __popc(t);
+        v[2] += __popc(s ^ t);
+        v[3] += __popc(s ^ tU) + __popc(s ^ tR);
+        v[4] += __popc(s ^ sU) + __popc(s ^ sR);
+    };
+    const uint32_t rlo = g.own_lo, rhi = g.own_lo + g.Hloc;
+    if constexpr (ROWS) {
+        const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const uint32_t f = warp * 32u, dr = fdiv((uint32_t)BLOCK, g.dw), dc = (uint32_t)BLOCK - dr * Wr;
+        uint32_t rho = rlo + fdiv(f, g.dw);
+        uint32_t c0 = f - (rho - rlo) * Wr;
+        while (rho < rhi) {
+            const uint32_t c = c0 + lane, row = rho * Wr;
+            add(row + c, (rho + 1 == g.R && g.wrap ? 0 : row + Wr) + c, row + (c + 1 == Wr ? 0 : c + 1));
+            c0 += dc;
+            rho += dr;
+            if (c0 >= Wr) {
+                c0 -= Wr;
+                ++rho;
+            }
+        }
+    } else {
+        for (uint32_t x = rlo * Wr + threadIdx.x; x < rhi * Wr; x += BLOCK) {
+            const uint32_t rho = fdiv(x, g.dw), c = x - rho * Wr;
+            add(x, (rho + 1 == g.R && g.wrap ? 0 : rho + 1) * Wr + c, rho * Wr + (c + 1 == Wr ? 0 : c + 1));
+        }
+    }
+}
+
+// Adds the block's per-thread values v[f] into red and, from warp 0, the
+// signed sums off[f] + mul[f] * (sum of v[f]) into dst[f] (nullptr: skipped).
+template <int BLOCK, int NV>
+__device__ __forceinline__ void tile_reduce(const int (&v)[NV], long long (*red)[BLOCK / 32],
+                                            const long long (&off)[NV], const int (&mul)[NV],
+                                            long long* const (&dst)[NV]) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int f = 0; f < NV; ++f) {
+        const int r = warp_sum(v[f]);
+        if (lane == 0) red[f][warp] = r;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int f = 0; f < NV; ++f) {
+            long long r = lane < BLOCK / 32 ? red[f][lane] : 0;
+            r = warp_sum64(r);
+            if (lane == 0 && dst[f] != nullptr)
+                atomicAdd(reinterpret_cast<unsigned long long*>(dst[f]), (unsigned long long)(off[f] + mul[f] * r));
+        }
+    }
+    __syncthreads();
+}
+
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_batch(const __grid_constant__ BatchArgs a) {
     extern __shared__ uint32_t tile_mem[];
     __shared__ DrawParams P;
     __shared__ PhiloxPrefix pre[2][8];     // half-steps A and B of the current step
@@ -178,7 +305,7 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
     __shared__ uint32_t item_sh;
     __shared__ unsigned long long t0_sh, burn_sh;
     __shared__ uint32_t par_sh, k_sh;
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
     uint32_t (*q)[kQueueCap] = qbuf[warp];
 
     for (;;) {
@@ -230,48 +357,37 @@ __global__ void __launch_bounds__(BLOCK) k_batch(const __grid_constant__ BatchAr
         }
         __syncthreads();
         long long* partial = reinterpret_cast<long long*>(a.arena + B->scratch_off);
+        const TileGeom g{R, wrap, Wr, dw, L, r_base, own_lo, Hloc};
+        const long long n_own = (long long)Hloc * Wr * 32;   // sites in the tile's own rows
         for (uint32_t j = 0; j < k; ++j) {
             const uint32_t hs = (uint32_t)(2 * (t0 + j));
             fill_prefixes(pre[0], P, hs);
             if (tid >= 8 && tid < 16) pre[1][tid - 8] = philox_prefix_dev(P, hs + 1, (int)(tid - 8));
             __syncthreads();
-            tile_sweep<0, BLOCK>(sg, tu, sweep_lo, R, R, wrap, Wr, dw, L, r_base, hs, P, pre[0], q);
+            if (Wr % 32u == 0u) {
+                tile_sweep<0, BLOCK, true>(sg, tu, sweep_lo, R, g, P, pre[0], q);
+                __syncthreads();
+                tile_sweep<1, BLOCK, true>(tu, sg, sweep_lo, wrap ? R : R - 1, g, P, pre[1], q);
+            } else {
+                tile_sweep<0, BLOCK, false>(sg, tu, sweep_lo, R, g, P, pre[0], q);
+                __syncthreads();
+                tile_sweep<1, BLOCK, false>(tu, sg, sweep_lo, wrap ? R : R - 1, g, P, pre[1], q);
+            }
             __syncthreads();
-            tile_sweep<1, BLOCK>(tu, sg, sweep_lo, wrap ? R : R - 1, R, wrap, Wr, dw, L, r_base, hs + 1, P,
-                                 pre[1], q);
-            __syncthreads();
-            // sums over the tile's own rows
+            // The step's sums enter the statistics from the burn-in on, and the
+            // launch's last step gives the last observables; the sums of other
+            // burn-in steps are never read, so they are not formed.
+            if (t0 + j < burn_sh && j + 1 < k) continue;
             int v[kNumObs] = {0, 0, 0, 0, 0};
-            for (uint32_t x = own_lo * Wr + tid; x < (own_lo + Hloc) * Wr; x += BLOCK) {
-                const uint32_t rho = fdiv(x, dw), c = x - rho * Wr;
-                const uint32_t cr = rho * Wr + (c + 1 == Wr ? 0 : c + 1);
-                const uint32_t xu = (rho + 1 == R && wrap ? 0 : rho + 1) * Wr + c;
-                const uint32_t s = sg[x], t = tu[x];
-                const uint32_t sU = sg[xu], tU = tu[xu];
-                const uint32_t sR = (s >> 1) | (sg[cr] << 31), tR = (t >> 1) | (tu[cr] << 31);
-                v[0] += 2 * __popc(s) - 32;
-                v[1] += 2 * __popc(t) - 32;
-                v[2] += 32 - 2 * __popc(s ^ t);
-                v[3] += 64 - 2 * (__popc(s ^ tU) + __popc(s ^ tR));
-                v[4] += 64 - 2 * (__popc(s ^ sU) + __popc(s ^ sR));
-            }
-#pragma unroll
-            for (int f = 0; f < kNumObs; ++f) {
-                const int r = warp_sum(v[f]);
-                if (lane == 0) red[f][warp] = r;
-            }
-            __syncthreads();
-            if (warp == 0) {
-#pragma unroll
-                for (int f = 0; f < kNumObs; ++f) {
-                    long long r = lane < BLOCK / 32 ? red[f][lane] : 0;
-                    r = warp_sum64(r);
-                    if (lane == 0)
-                        atomicAdd(reinterpret_cast<unsigned long long*>(partial + j * kNumObs + f),
-                                  (unsigned long long)r);
-                }
-            }
-            __syncthreads();
+            if (Wr % 32u == 0u) tile_counts<BLOCK, true>(sg, tu, g, v);
+            else tile_counts<BLOCK, false>(sg, tu, g, v);
+            // M = 2 up - n, M_tau = 2 up - n, S_q = n - 2 disagreeing,
+            // S_J = 2 n - 2 disagreeing, C_nn = 2 n - 2 disagreeing
+            long long* const pj = partial + j * kNumObs;
+            const long long off[kNumObs] = {-n_own, -n_own, n_own, 2 * n_own, 2 * n_own};
+            const int mul[kNumObs] = {2, 2, -2, -2, -2};
+            long long* const dst[kNumObs] = {pj, pj + 1, pj + 2, pj + 3, pj + 4};
+            tile_reduce<BLOCK, kNumObs>(v, red, off, mul, dst);
         }
         // write the tile's rows of sigma (other buffer) and tau
         uint32_t* sig_out = reinterpret_cast<uint32_t*>(a.arena + B->sigma_off[par ^ 1u]);
@@ -640,7 +756,12 @@ int shk_batch_configure(shk_batch* b, int steps_per_launch, int block_threads, i
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t static_smem = sizeof(DrawParams) + (size_t)(block_threads / 32) * (kBatchQueueFields * kQueueCap * 4 + kNumObs * 8) + 64;
+    cudaFuncAttributes fa = {};
+    const cudaError_t fe = cudaFuncGetAttributes(
+        &fa, block_threads == 128 ? (const void*)k_batch<128> : block_threads == 512 ? (const void*)k_batch<512>
+                                                                                    : (const void*)k_batch<256>);
+    if (fe != cudaSuccess) return bfail(b, SHK_ECUDA, "shk_batch_configure: %s", cudaGetErrorString(fe));
+    const size_t static_smem = fa.sharedSizeBytes;
     if (b->smem_bytes + static_smem > (size_t)optin)
         return bfail(b, SHK_EINVAL, "shk_batch_configure: a tile needs %zu bytes of shared memory (limit %d); lower tile_sites or steps_per_launch",
                      b->smem_bytes + static_smem, optin);
