@@ -342,7 +342,6 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_batch(const __grid_cons
         const int32_t r_base = wrap ? 0 : (int32_t)r0 - (int32_t)k;
         const FastDiv dw = B->div_wr;
         const uint32_t own_lo = wrap ? 0 : k;           // local rows of the tile itself
-        const uint32_t sweep_lo = wrap ? 0 : 1;
         {
             const uint32_t* src = reinterpret_cast<const uint32_t*>(&B->P);
             uint32_t* dstp = reinterpret_cast<uint32_t*>(&P);
@@ -364,14 +363,18 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_batch(const __grid_cons
             fill_prefixes(pre[0], P, hs);
             if (tid >= 8 && tid < 16) pre[1][tid - 8] = philox_prefix_dev(P, hs + 1, (int)(tid - 8));
             __syncthreads();
+            // Rows that later steps and the outputs still need: tau of step j
+            // on [j + 1, R - j), sigma on [j + 1, R - 1 - j) (all rows when
+            // the tile is the whole torus).
+            const uint32_t lo = wrap ? 0 : j + 1, hiA = wrap ? R : R - j, hiB = wrap ? R : R - 1 - j;
             if (Wr % 32u == 0u) {
-                tile_sweep<0, BLOCK, true>(sg, tu, sweep_lo, R, g, P, pre[0], q);
+                tile_sweep<0, BLOCK, true>(sg, tu, lo, hiA, g, P, pre[0], q);
                 __syncthreads();
-                tile_sweep<1, BLOCK, true>(tu, sg, sweep_lo, wrap ? R : R - 1, g, P, pre[1], q);
+                tile_sweep<1, BLOCK, true>(tu, sg, lo, hiB, g, P, pre[1], q);
             } else {
-                tile_sweep<0, BLOCK, false>(sg, tu, sweep_lo, R, g, P, pre[0], q);
+                tile_sweep<0, BLOCK, false>(sg, tu, lo, hiA, g, P, pre[0], q);
                 __syncthreads();
-                tile_sweep<1, BLOCK, false>(tu, sg, sweep_lo, wrap ? R : R - 1, g, P, pre[1], q);
+                tile_sweep<1, BLOCK, false>(tu, sg, lo, hiB, g, P, pre[1], q);
             }
             __syncthreads();
             // The step's sums enter the statistics from the burn-in on, and the
