@@ -129,24 +129,27 @@ def test_full_phase_diagram_batch_spot_checks(orc):
         assert np.array_equal(b.read_spins(i, 1).reshape(-1), tau), i
 
 
-def test_phase_diagram_batch_against_the_oracle(orc):
-    """The batched configuration at its full size and in the benchmark's tuned
-    launch shape (2 steps per launch, 256 threads, 2^17-site tiles): all 1024
-    lattices of the phase diagram (L log-uniform in {32, ..., 2048}, one
-    (q, J) cell each) run 56 steps with a 16-step burn-in.
+@pytest.mark.parametrize("k,block,tile_sites", [(4, 512, 1 << 18), (2, 256, 1 << 17)])
+def test_phase_diagram_batch_against_the_oracle(orc, k, block, tile_sites):
+    """The batched configuration at its full size, in the launch shape the
+    benchmark's autotuner picks (4 steps per launch, 512 threads, 2^18-site
+    tiles) and in a second one with smaller tiles and more halo rows (2
+    steps, 256 threads, 2^17 sites): all 1024 lattices of the phase diagram
+    (L log-uniform in {32, ..., 2048}, one (q, J) cell each) run 56 steps
+    with a 16-step burn-in.
     - Every lattice with L <= 256 is recomputed by the oracle from its random
       start: final sigma and tau, the five sums of the last step, and the
       eleven exact statistics of the 40 measured steps (Eq. fact applied to
       each lattice on its own, as in the task-parallel runs of the paper).
     - 48 larger lattices (16 each of L = 512, 1024, 2048, whose tiles carry
       recomputed halo rows) are spot-checked over one launch: the oracle takes
-      the GPU's sigma after step 56 and runs steps 56 and 57; sigma, tau and
-      the last step's sums must agree after the GPU's next launch.
+      the GPU's sigma after step 56 and runs the next launch's k steps; sigma,
+      tau and the last step's sums must agree after the GPU's next launch.
     The oracle runs on every host core (its C calls release the interpreter
     lock); it shares no code with the GPU path."""
     w = workloads.phase_diagram_batch()
-    n, burn, k = 56, 16, 2
-    b = Batch(w["L"], w["q"], w["J"], w["seed"], w["lattice_id"]).configure(k, 256, 1 << 17)
+    n, burn = 56, 16
+    b = Batch(w["L"], w["q"], w["J"], w["seed"], w["lattice_id"]).configure(k, block, tile_sites)
     b.init("random", init_seed=w["init_seed"])
     b.run(n, burn_in=burn)
     stats, last = b.read_stats(), b.read_observables()
