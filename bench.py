@@ -693,8 +693,8 @@ def bench_l_sweep(dev, stream) -> dict:
                         "(sums of the last step kept on the device)", "rows": rows}
 
 
-def bench_serving(dev, stream, n_jobs: int = 10_000, sub_jobs: int = 1000, steps_per_launch: int = 2,
-                  launches_per_tick: int = 16):
+def bench_serving(dev, stream, n_jobs: int = 10_000, sub_jobs: int = 1000, steps_per_launch: int = 4,
+                  launches_per_tick: int = 8, block_threads: int = 512, tile_sites: int = 1 << 18):
     """Continuous batching on the serving stream: its first n_jobs jobs (the
     whole configured stream by default: 10^4 jobs, Poisson arrivals at a mean
     of 200/s, L log-uniform in [64, 4096], steps log-uniform in [10^3, 10^5],
@@ -711,8 +711,8 @@ def bench_serving(dev, stream, n_jobs: int = 10_000, sub_jobs: int = 1000, steps
     def one(n, rate, seed=5):
         w = workloads.serving_stream(n_jobs=n, rate_per_s=rate, seed=seed)
         srv = Server(max_slots=1024, arena_bytes=8 << 30, hbm_budget=96 << 30, device=dev, stream=stream)
-        srv.configure(steps_per_launch=steps_per_launch, launches_per_tick=launches_per_tick, block_threads=256,
-                      tile_sites=1 << 18)
+        srv.configure(steps_per_launch=steps_per_launch, launches_per_tick=launches_per_tick,
+                      block_threads=block_threads, tile_sites=tile_sites)
         r = replay_stream(srv, w["jobs"], w["arrivals"])
         srv.close()
         assert all(x["status"] == 0 for x in r["results"])
@@ -733,10 +733,11 @@ def bench_serving(dev, stream, n_jobs: int = 10_000, sub_jobs: int = 1000, steps
             "jobs": n_jobs, "unit": UNIT, "value": sat["throughput"], "p50_latency_s": sat["p50_latency_s"],
             "p99_latency_s": sat["p99_latency_s"], "saturated": sat, "sub_saturation": sub,
             "steps_per_launch": steps_per_launch, "launches_per_tick": launches_per_tick,
+            "block_threads": block_threads, "tile_sites": tile_sites,
             "capacity_jobs_per_s": capacity_jobs_per_s,
-            "note": "the stream offers about 7x the capacity, so the saturated latencies measure the backlog; "
-                    "the sub-saturation replays (other seeds of the same job distribution) give the latency "
-                    "of a steady state"}
+            "note": f"the stream offers about {200.0 / capacity_jobs_per_s:.1f}x the capacity, so the saturated "
+                    "latencies measure the backlog; the sub-saturation replays (other seeds of the same job "
+                    "distribution) give the latency of a steady state"}
 
 
 def run_kernel_case(spec: str) -> int:
