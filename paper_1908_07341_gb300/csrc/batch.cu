@@ -114,10 +114,9 @@ struct TileGeom {
 };
 
 // Draws rows [rlo, rhi) of dst (local row index) from src in shared memory.
-// HALF 0 reads the row below
-// (rho - 1), HALF 1 the row above (rho + 1); the left/right neighbour wraps
-// within the row.  Random numbers use the global block index (global row
-// g = (r_base + rho) mod L).
+// HALF 0 reads the row below (rho - 1), HALF 1 the row above (rho + 1); the
+// left/right neighbour wraps within the row.  Random numbers use the global
+// block index (global row g = (r_base + rho) mod L).
 // ROWS: the lattice's rows are whole multiples of 32 words (L a multiple of
 // 1024), so the 32 lanes of a warp always cover 32 consecutive words of one
 // row: the row, its neighbour row and its global row are the same for the
