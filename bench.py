@@ -693,8 +693,8 @@ def bench_l_sweep(dev, stream) -> dict:
                         "(sums of the last step kept on the device)", "rows": rows}
 
 
-def bench_serving(dev, stream, n_jobs: int = 10_000, sub_jobs: int = 1000, steps_per_launch: int = 4,
-                  launches_per_tick: int = 8, block_threads: int = 512, tile_sites: int = 1 << 18):
+def bench_serving(dev, stream, n_jobs: int = 10_000, sub_jobs: int = 1000, steps_per_launch: int = 2,
+                  launches_per_tick: int = 16, block_threads: int = 256, tile_sites: int = 1 << 17):
     """Continuous batching on the serving stream: its first n_jobs jobs (the
     whole configured stream by default: 10^4 jobs, Poisson arrivals at a mean
     of 200/s, L log-uniform in [64, 4096], steps log-uniform in [10^3, 10^5],

@@ -24,7 +24,7 @@ def _gpu():
 
 
 # the serving benchmark's launch shape (bench.py, bench_serving)
-BENCH_SHAPE = dict(steps_per_launch=4, launches_per_tick=8, block_threads=512, tile_sites=1 << 18)
+BENCH_SHAPE = dict(steps_per_launch=2, launches_per_tick=16, block_threads=256, tile_sites=1 << 17)
 
 JOBS = [dict(L=64, q=1.0, J=0.25, seed=1, lattice_id=0, n_steps=37, burn_in=10),
         dict(L=128, q=0.5, J=0.5, seed=2, lattice_id=1, n_steps=16, burn_in=0),
@@ -171,8 +171,8 @@ def test_result_log_lines(tmp_path):
 def test_serving_stream_jobs_spot_checked_against_the_oracle(orc):
     """Jobs of the serving workload itself (the first 300 jobs of the Poisson
     stream, L log-uniform in [64, 4096], steps log-uniform in [10^3, 10^5]) in
-    the benchmark's launch shape (4 steps per launch, 8 launches per tick,
-    512 threads, 2^18-site tiles), all in one mix; the smallest ones (the
+    the benchmark's launch shape (2 steps per launch, 16 launches per tick,
+    256 threads, 2^17-site tiles), all in one mix; the smallest ones (the
     oracle finishes them in seconds) are recomputed by the oracle: exact
     statistics after burn-in, last-step sums and the hash of the final sigma."""
     from paper_1908_07341_gb300 import workloads
@@ -207,14 +207,14 @@ def test_serving_stream_mixed_jobs_against_the_oracle(orc):
     """40 jobs of the serving workload (the first 400 jobs of the Poisson
     stream: L log-uniform in [64, 4096], q, J uniform, steps log-uniform in
     [10^3, 10^5], seed 5, lattice id = job index) in one mix, in the
-    benchmark's launch shape (4 steps per launch, 8 launches per tick, 512
-    threads, 2^18-site tiles):
+    benchmark's launch shape (2 steps per launch, 16 launches per tick, 256
+    threads, 2^17-site tiles):
     - 32 jobs spread over the whole range of L (the largest included) are
       spot-checked in flight after a tick of that shape: the test reads each
       job's sigma and step count between ticks (shk_server_read_job), the
-      server runs one tick of a single launch (4 steps, every job in the mix
+      server runs one tick of a single launch (2 steps, every job in the mix
       advancing), sigma and tau are read again, and the oracle runs the same
-      four steps from the GPU's sigma; the checked jobs are then cancelled;
+      two steps from the GPU's sigma; the checked jobs are then cancelled;
     - the 8 cheapest jobs run to completion and are recomputed by the oracle
       from their random starts: the exact statistics after burn-in, the last
       step's sums and the hash of the final sigma."""
@@ -227,7 +227,8 @@ def test_serving_stream_mixed_jobs_against_the_oracle(orc):
     rest = sorted((i for i in range(len(jobs)) if i not in full), key=lambda i: (jobs[i]["L"], i))
     spot = sorted({rest[int(round(x))] for x in np.linspace(0, len(rest) - 1, 32)})
     assert len(spot) == 32 and max(jobs[i]["L"] for i in spot) == max(j["L"] for j in jobs)
-    assert all(jobs[i]["n_steps"] > 36 for i in spot)
+    k = BENCH_SHAPE["steps_per_launch"]
+    assert all(jobs[i]["n_steps"] > 32 + k for i in spot)
     srv = Server(max_slots=64, arena_bytes=1 << 30).configure(**BENCH_SHAPE)
     ids = {srv.submit(**jobs[i]): i for i in sorted(set(full) | set(spot))}
     job_id = {i: jid for jid, i in ids.items()}
@@ -249,13 +250,13 @@ def test_serving_stream_mixed_jobs_against_the_oracle(orc):
         (s0, t0) = before[i]
         s = s0.reshape(-1).copy()
         t = np.zeros_like(s)
-        obs = orc.run(s, t, j["L"], j["q"], j["J"], j["seed"], j["lattice_id"], t0, 4)
+        obs = orc.run(s, t, j["L"], j["q"], j["J"], j["seed"], j["lattice_id"], t0, k)
         return i, t0, s, t, obs
 
     with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
         for i, t0, s, t, obs in ex.map(spot_check, spot):
             (s1, t1), tau1 = after[i]
-            assert t0 == 32 and t1 == 36, (i, t0, t1)
+            assert t0 == 32 and t1 == 32 + k, (i, t0, t1)
             assert np.array_equal(s1.reshape(-1), s), i
             assert np.array_equal(tau1.reshape(-1), t), i
     for _ in range(100_000):
