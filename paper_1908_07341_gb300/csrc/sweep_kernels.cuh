@@ -205,12 +205,24 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_i8a(const SweepArgs a) {
 
 // ------------------------------------------------------------ two-phase sweeps
 //
-// Each warp owns a ring of kQueueCap parked blocks in shared memory (structure
-// of arrays: block index, undecided mask, decided-up mask and the three input
-// words).  Blocks still undecided after Philox calls 0 and 1 wait there; once
-// 32 are waiting the warp continues them together from call 2 (draw_rest).
+// Each warp owns a ring of kQueueCap parked blocks in shared memory.  Blocks
+// still undecided after Philox calls 0 and 1 wait there; once 32 are waiting
+// the warp continues them together from call 2 (draw_rest).
 
-constexpr int kQueueFields = 6;
+// One parked block, 32 bytes: block index, undecided mask, decided-up mask and
+// source word in one 16-byte store, the two field-neighbour words in an 8-byte
+// one (two shared-memory instructions per parking warp instead of six).
+struct QueueEntry {
+    uint4 a;   // w, und, up, S
+    uint2 b;   // N1, N2
+    uint2 pad;
+};
+
+__device__ __forceinline__ void queue_put(QueueEntry& e, uint32_t w, uint32_t und, uint32_t up, uint32_t S,
+                                          uint32_t N1, uint32_t N2) {
+    e.a = make_uint4(w, und, up, S);
+    e.b = make_uint2(N1, N2);
+}
 
 template <int HALF, int LAYOUT>
 __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uint32_t up, uint32_t S,
@@ -229,19 +241,21 @@ __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uin
 
 // Continues the `count` (<= 32) oldest parked blocks; all lanes call it.
 template <int HALF, int LAYOUT, class PP>
-__device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, uint32_t (*q)[kQueueCap],
+__device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, QueueEntry* q,
                                             uint32_t head, int count, bool cnn, int (&acc)[4]) {
     const uint32_t lane = threadIdx.x & 31;
     const bool has = (int)lane < count;
     const uint32_t i = (head + lane) & (kQueueCap - 1);
     uint32_t w = 0, und = 0, up = 0, S = 0, N1 = 0, N2 = 0;
     if (has) {
-        w = q[0][i];
-        und = q[1][i];
-        up = q[2][i];
-        S = q[3][i];
-        N1 = q[4][i];
-        N2 = q[5][i];
+        const uint4 x = q[i].a;
+        const uint2 y = q[i].b;
+        w = x.x;
+        und = x.y;
+        up = x.z;
+        S = x.w;
+        N1 = y.x;
+        N2 = y.y;
     }
     const BlockClass k = block_class(S, N1, N2);
     const uint32_t res = draw_rest_pre(k, w, und, up, a.pre, P);
@@ -251,12 +265,12 @@ __device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, uin
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     pdl_begin();
-    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const DrawParams& P = a.P;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
-    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    QueueEntry* q = qbuf[threadIdx.x >> 5];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
     int acc[4] = {0, 0, 0, 0};
@@ -281,12 +295,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {
             const uint32_t i = (head + count + __popc(mask & below)) & (kQueueCap - 1);
-            q[0][i] = w;
-            q[1][i] = und;
-            q[2][i] = up;
-            q[3][i] = S;
-            q[4][i] = N1;
-            q[5][i] = N2;
+            queue_put(q[i], w, und, up, S, N1, N2);
         } else {
             finish_block<HALF, LAYOUT>(a, w, up, S, N1, N2, cnn, acc);
         }
@@ -334,13 +343,13 @@ __device__ __forceinline__ void load_words(const uint32_t* __restrict__ pl, uint
 template <int HALF, int V, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_qv(const SweepArgs a) {
     pdl_begin();
-    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const DrawParams& P = a.P;
     const uint32_t* __restrict__ src = static_cast<const uint32_t*>(a.src);
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t stride = ((gridDim.x * blockDim.x) >> 5) * 32;
-    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    QueueEntry* q = qbuf[threadIdx.x >> 5];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
     int acc[4] = {0, 0, 0, 0};
@@ -376,12 +385,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_qv(const SweepArgs a) {
             const uint32_t mask = __ballot_sync(0xffffffffu, parked);
             if (parked) {
                 const uint32_t i = (head + count + __popc(mask & below)) & (kQueueCap - 1);
-                q[0][i] = w;
-                q[1][i] = und;
-                q[2][i] = up;
-                q[3][i] = S[k];
-                q[4][i] = N1[k];
-                q[5][i] = N2;
+                queue_put(q[i], w, und, up, S[k], N1[k], N2);
             } else {
                 finish_block<HALF, kBitpack>(a, w, up, S[k], N1[k], N2, cnn, acc);
             }
@@ -464,11 +468,11 @@ __device__ __forceinline__ uint32_t edge_bit(const void* src, uint32_t row, uint
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) {
     pdl_begin();
-    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    uint32_t (*q)[kQueueCap] = qbuf[threadIdx.x >> 5];
+    QueueEntry* q = qbuf[threadIdx.x >> 5];
     const DrawParams& P = a.P;
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
@@ -527,12 +531,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) 
             const uint32_t mask = __ballot_sync(0xffffffffu, parked);
             if (parked) {
                 const uint32_t qi = (head + count + __popc(mask & below)) & (kQueueCap - 1);
-                q[0][qi] = w;
-                q[1][qi] = und;
-                q[2][qi] = up;
-                q[3][qi] = S;
-                q[4][qi] = N1;
-                q[5][qi] = N2;
+                queue_put(q[qi], w, und, up, S, N1, N2);
             } else {
                 finish_block<HALF, LAYOUT>(a, w, up, S, N1, N2, cnn, acc);
             }
@@ -568,14 +567,14 @@ template <int HALF, int LAYOUT, int BLOCK, int MINB, int DEPTH>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepArgs a) {
     pdl_begin();
     constexpr int NW = RowWords<LAYOUT>::kWords;
-    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const DrawParams& P = a.P;
     __shared__ __align__(16) uint32_t ring[BLOCK / 32][DEPTH][32 * NW];
     __shared__ __align__(16) uint32_t ring_edge[BLOCK / 32][DEPTH][4];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    uint32_t (*q)[kQueueCap] = qbuf[wib];
+    QueueEntry* q = qbuf[wib];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
     int acc[4] = {0, 0, 0, 0};
@@ -670,12 +669,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
             const uint32_t mask = __ballot_sync(0xffffffffu, parked);
             if (parked) {
                 const uint32_t qi = (head + count + __popc(mask & below)) & (kQueueCap - 1);
-                q[0][qi] = w;
-                q[1][qi] = und;
-                q[2][qi] = up;
-                q[3][qi] = S;
-                q[4][qi] = N1;
-                q[5][qi] = N2;
+                queue_put(q[qi], w, und, up, S, N1, N2);
             } else {
                 finish_block<HALF, LAYOUT>(a, w, up, S, N1, N2, cnn, acc);
             }
@@ -711,7 +705,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
 template <int HALF, int BLOCK, int MINB, int DEPTH>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArgs a) {
     pdl_begin();
-    __shared__ uint32_t qbuf[BLOCK / 32][kQueueFields][kQueueCap];
+    __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     __shared__ __align__(128) uint32_t ring[BLOCK / 32][DEPTH][256];       // 1024 bytes per row
     __shared__ uint32_t ring_edge[BLOCK / 32][DEPTH];                      // the word holding the edge byte
     __shared__ __align__(8) uint64_t bar[BLOCK / 32][DEPTH];
@@ -719,7 +713,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArg
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    uint32_t (*q)[kQueueCap] = qbuf[wib];
+    QueueEntry* q = qbuf[wib];
     if (a.zero_slot != nullptr && blockIdx.x == 0 && threadIdx.x < kNumObs) a.zero_slot[threadIdx.x] = 0;
     const bool cnn = HALF == 0 && a.obs_prev != nullptr;
     int acc[4] = {0, 0, 0, 0};
@@ -820,12 +814,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArg
             const uint32_t mask = __ballot_sync(0xffffffffu, parked);
             if (parked) {
                 const uint32_t qi = (head + count + __popc(mask & below)) & (kQueueCap - 1);
-                q[0][qi] = w;
-                q[1][qi] = und;
-                q[2][qi] = up;
-                q[3][qi] = S;
-                q[4][qi] = N1;
-                q[5][qi] = N2;
+                queue_put(q[qi], w, und, up, S, N1, N2);
             } else {
                 finish_block<HALF, kInt8>(a, w, up, S, N1, N2, cnn, acc);
             }
