@@ -44,7 +44,10 @@ namespace shk {
 constexpr int kMaxStepsPerLaunch = 32;
 constexpr int kStatFields = SHK_NSTATS;
 static_assert(SHK_NSTATS == 11, "statistics layout");
-constexpr int kBatchQueueFields = 7;   // w, und, up, S, N1, N2, local index
+// A parked block: w, und, up, S | N1, N2, local index (two 16-byte stores)
+struct BatchQueueEntry {
+    uint4 a, b;
+};
 
 struct BatchLattice {
     uint32_t L, Wr;             // side, words per row
@@ -126,7 +129,7 @@ struct TileGeom {
 template <int HALF, int BLOCK, bool ROWS>
 __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, uint32_t rlo, uint32_t rhi,
                                            const TileGeom& g, const DrawParams& P, const PhiloxPrefix (&pre)[8],
-                                           uint32_t (*q)[kQueueCap]) {
+                                           BatchQueueEntry* q) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t below = (1u << lane) - 1u;
     const uint32_t Wr = g.Wr, R = g.R;
@@ -137,7 +140,8 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
         const uint32_t e = (head + lane) & (kQueueCap - 1);
         uint32_t w = 0, und = 0, up = 0, S = 0, N1 = 0, N2 = 0, i = 0;
         if (has) {
-            w = q[0][e]; und = q[1][e]; up = q[2][e]; S = q[3][e]; N1 = q[4][e]; N2 = q[5][e]; i = q[6][e];
+            const uint4 x = q[e].a, y = q[e].b;
+            w = x.x; und = x.y; up = x.z; S = x.w; N1 = y.x; N2 = y.y; i = y.z;
         }
         const uint32_t res = draw_rest_pre(block_class(S, N1, N2), w, und, up, pre, P);
         if (has) dst[i] = res;
@@ -152,7 +156,8 @@ __device__ __forceinline__ void tile_sweep(const uint32_t* src, uint32_t* dst, u
         const uint32_t mask = __ballot_sync(0xffffffffu, parked);
         if (parked) {
             const uint32_t e = (head + count + __popc(mask & below)) & (kQueueCap - 1);
-            q[0][e] = w; q[1][e] = und; q[2][e] = up; q[3][e] = S; q[4][e] = N1; q[5][e] = N2; q[6][e] = i;
+            q[e].a = make_uint4(w, und, up, S);
+            q[e].b = make_uint4(N1, N2, i, 0u);
         } else if (valid != 0u) {
             dst[i] = up;
         }
@@ -299,13 +304,13 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_batch(const __grid_cons
     extern __shared__ uint32_t tile_mem[];
     __shared__ DrawParams P;
     __shared__ PhiloxPrefix pre[2][8];     // half-steps A and B of the current step
-    __shared__ uint32_t qbuf[BLOCK / 32][kBatchQueueFields][kQueueCap];
+    __shared__ BatchQueueEntry qbuf[BLOCK / 32][kQueueCap];
     __shared__ long long red[kNumObs][BLOCK / 32];
     __shared__ uint32_t item_sh;
     __shared__ unsigned long long t0_sh, burn_sh;
     __shared__ uint32_t par_sh, k_sh;
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
-    uint32_t (*q)[kQueueCap] = qbuf[warp];
+    BatchQueueEntry* q = qbuf[warp];
 
     for (;;) {
         if (tid == 0) item_sh = atomicAdd(&a.state->next, 1u);
