@@ -224,6 +224,30 @@ __device__ __forceinline__ void queue_put(QueueEntry& e, uint32_t w, uint32_t un
     e.b = make_uint2(N1, N2);
 }
 
+// The four int8 spins of every 4-bit group of a result word (unpack4 of
+// 0..15), one table per CTA: the int8 sweeps that store through finish_block
+// fill it at entry (unpack_table_init) and expand a word with 8 lookups.
+__shared__ uint32_t g_unpack_table[16];
+
+template <int LAYOUT>
+__device__ __forceinline__ void unpack_table_init() {
+    if constexpr (LAYOUT == kInt8) {
+        if (threadIdx.x < 16) g_unpack_table[threadIdx.x] = unpack4(threadIdx.x);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void unpack32_table(uint32_t bits, uint4& lo, uint4& hi) {
+    lo.x = g_unpack_table[bits & 0xFu];
+    lo.y = g_unpack_table[(bits >> 4) & 0xFu];
+    lo.z = g_unpack_table[(bits >> 8) & 0xFu];
+    lo.w = g_unpack_table[(bits >> 12) & 0xFu];
+    hi.x = g_unpack_table[(bits >> 16) & 0xFu];
+    hi.y = g_unpack_table[(bits >> 20) & 0xFu];
+    hi.z = g_unpack_table[(bits >> 24) & 0xFu];
+    hi.w = g_unpack_table[bits >> 28];
+}
+
 template <int HALF, int LAYOUT>
 __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uint32_t up, uint32_t S,
                                              uint32_t N1, uint32_t N2, bool cnn, int (&acc)[4]) {
@@ -231,7 +255,7 @@ __device__ __forceinline__ void finish_block(const SweepArgs& a, uint32_t w, uin
         *checked(static_cast<uint32_t*>(a.dst), w, a.nblocks, SHK_SITE) = up;
     } else {
         uint4 lo, hi;
-        unpack32(up, lo, hi);
+        unpack32_table(up, lo, hi);
         uint4* q4 = reinterpret_cast<uint4*>(a.dst);
         *checked(q4, 2 * (uint64_t)w, 2 * (uint64_t)a.nblocks, SHK_SITE) = lo;
         *checked(q4, 2 * (uint64_t)w + 1, 2 * (uint64_t)a.nblocks, SHK_SITE) = hi;
@@ -265,6 +289,7 @@ __device__ __forceinline__ void drain_queue(const SweepArgs& a, const PP& P, Que
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_q(const SweepArgs a) {
     pdl_begin();
+    unpack_table_init<LAYOUT>();
     __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const DrawParams& P = a.P;
     const uint32_t lane = threadIdx.x & 31;
@@ -468,6 +493,7 @@ __device__ __forceinline__ uint32_t edge_bit(const void* src, uint32_t row, uint
 template <int HALF, int LAYOUT, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip(const SweepArgs a) {
     pdl_begin();
+    unpack_table_init<LAYOUT>();
     __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -566,6 +592,7 @@ struct RowWords {
 template <int HALF, int LAYOUT, int BLOCK, int MINB, int DEPTH>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepArgs a) {
     pdl_begin();
+    unpack_table_init<LAYOUT>();
     constexpr int NW = RowWords<LAYOUT>::kWords;
     __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     const DrawParams& P = a.P;
@@ -705,6 +732,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_async(const SweepAr
 template <int HALF, int BLOCK, int MINB, int DEPTH>
 __global__ void __launch_bounds__(BLOCK, MINB) k_sweep_strip_bulk(const SweepArgs a) {
     pdl_begin();
+    unpack_table_init<kInt8>();
     __shared__ QueueEntry qbuf[BLOCK / 32][kQueueCap];
     __shared__ __align__(128) uint32_t ring[BLOCK / 32][DEPTH][256];       // 1024 bytes per row
     __shared__ uint32_t ring_edge[BLOCK / 32][DEPTH];                      // the word holding the edge byte
